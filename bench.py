@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Throughput of the SoA particle hot path on B300, one JSON line on stdout.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl soax|reference] [--no-rows]
+
+Workload (one "step" of this benchmark): the 16,777,216-particle set {i32 id, f64 pos[3],
+f32 vel[3]} in the ABC flow (A = B = C = 1, tau = 0.1, dt = 1e-3); one bench step is one
+sort interval: 10 midpoint-RK2 steps (one launch and one pass over the planes each)
+followed by the cell sort on a 32^3 grid (keys, stable radix sort, permute-gather of every
+plane).  K bench steps = 10 K RK2 steps; the default K = 100 is the full 1000-step run.
+
+Metric: particle-steps/s (whole job, all ranks).  The dominant kernel is the RK2 step; its
+roofline is HBM bandwidth at 72 algorithmic bytes per particle-step (pos 24 + vel 12 bytes
+read and written), against the measured copy bandwidth in MEASURED_PEAKS.json.
+
+Also measured in the same run ("rows"): the AoS <-> SoA round trip and the AoS step on the
+same set, the sort's share, the forward+adjoint of the 1M-particle K = 1000 problem against
+the plain step, and the batched persistent launch over 512 uneven ensembles against 512
+separate plain launches per step (a few steps each, reported per particle-step).
+
+--impl reference times the CPU oracle on the host cores on a bounded sample of the same
+workload (the only other place that runs oracle/ besides the cpu_baseline leg).
+
+Multi-GPU (torchrun): every rank advances its own replica of the workload (weak scaling,
+no collective on the data path); time = max over ranks; value = all ranks' particle-steps
+/ that time.
+"""
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import soax_inputs  # noqa: E402
+
+WL = soax_inputs.WORKLOADS["sorted_n16M"]
+RK2_PER_STEP = WL["sort_every"]
+BYTES_PER_PARTICLE_STEP = 72  # pos 3 x f64 + vel 3 x f32, read and written
+METRIC = "particle-steps/s"
+L2_BYTES = 126 * 2 ** 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="soax", choices=["soax", "reference"])
+    ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
+    ap.add_argument("--n", type=int, default=WL["n"], help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def aggregate(local_units, local_seconds, device=None):
+    """(sum of units over ranks, max of seconds over ranks); works for any backend."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_units), float(local_seconds)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    s = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6400.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1710_03462_b300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of kernel from the committed ncu summary, if it was taken on
+    the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            j = json.load(fh)
+        e = j.get(kernel)
+        if e and e.get("source_hash") == source_hash():
+            return float(e["dram_bytes_per_launch_full_size"])
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle as the reference arm: each bench step is a bounded sample of the
+    workload (a quarter of the particles: 10 RK2 steps + the cell sort of that sample)."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    cores = os.cpu_count() or 1
+    ns = min(args.n, 1 << 22)
+    d = soax_inputs.basic_set(ns, WL["seed"])
+    pos = [p.copy() for p in d["pos"]]
+    vel = [v.copy() for v in d["vel"]]
+    ids = d["id"][0].copy()
+
+    def one():
+        nonlocal pos, vel, ids
+        oracle.step_soa(pos, vel, WL["A"], WL["B"], WL["C"], WL["tau"], WL["dt"], RK2_PER_STEP, threads=cores)
+        keys = oracle.cell_keys(*pos, WL["grid"])
+        perm, _ = oracle.stable_argsort(keys)
+        out = oracle.permute([ids] + pos + vel, perm)
+        ids, pos, vel = out[0], out[1:4], out[4:7]
+
+    steps = max(1, min(args.steps, 5))
+    for _ in range(max(0, min(args.warmup, 1))):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    el = time.perf_counter() - t0
+    value = ns * RK2_PER_STEP * steps / el
+    sample = f"{ns} of {args.n} particles x {RK2_PER_STEP} RK2 steps + cell sort, {steps} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": el / steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sorted_n16M", "n": args.n, "grid": WL["grid"], "sort_every": RK2_PER_STEP},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(n):
+    """The oracle on the host cores: 10 RK2 steps + one cell sort over a bounded sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    ns = min(n, 1 << 22)
+    d = soax_inputs.basic_set(ns, WL["seed"])
+    pos = [p.copy() for p in d["pos"]]
+    vel = [v.copy() for v in d["vel"]]
+    t0 = time.perf_counter()
+    oracle.step_soa(pos, vel, WL["A"], WL["B"], WL["C"], WL["tau"], WL["dt"], RK2_PER_STEP, threads=cores)
+    keys = oracle.cell_keys(*pos, WL["grid"])
+    perm, _ = oracle.stable_argsort(keys)
+    oracle.permute(d["id"] + pos + vel, perm)
+    el = time.perf_counter() - t0
+    return {"value": ns * RK2_PER_STEP / el, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{ns} particles x {RK2_PER_STEP} RK2 steps + one cell sort (one bench step on a quarter "
+                      f"of the set), {el:.1f} s"}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_soax(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1710_03462_b300 as sx
+
+    rank, local, world = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    n = args.n
+    flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
+    d = soax_inputs.basic_set(n, WL["seed"] + rank)
+    p = sx.Particles(sx.BASIC_SCHEMA, n, device=dev)
+    p.load(d)
+    ws = p.sort_workspace(WL["grid"])
+    stream = torch.cuda.current_stream(dev)
+
+    def bench_step(ev=None):
+        for k in range(RK2_PER_STEP):
+            if ev is not None:
+                ev[0][k].record(stream)
+            p.step(flow, 1)
+            if ev is not None:
+                ev[1][k].record(stream)
+        if ev is not None:
+            ev[2].record(stream)
+        p.sort_by_cell(WL["grid"], ws)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize(dev)
+    evs = [([torch.cuda.Event(enable_timing=True) for _ in range(RK2_PER_STEP)],
+            [torch.cuda.Event(enable_timing=True) for _ in range(RK2_PER_STEP)],
+            torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index) as clk:
+        start.record(stream)
+        for s in range(args.steps):
+            bench_step(evs[s])
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    elapsed = start.elapsed_time(stop) / 1e3
+    step_ms = [evs[s][0][k].elapsed_time(evs[s][1][k]) for s in range(args.steps) for k in range(RK2_PER_STEP)]
+    sort_ms = [evs[s][2].elapsed_time(evs[s][3]) for s in range(args.steps)]
+    units = n * RK2_PER_STEP * args.steps
+    tot_units, max_el = aggregate(units, elapsed, dev)
+
+    # e2e through the public API with host buffers: the state goes up and comes back
+    # every bench step (pinned memory, one async copy per plane).
+    host = {k: [torch.from_numpy(a).pin_memory() for a in v] for k, v in d.items()}
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = sum(t.numel() * t.element_size() for v in host.values() for t in v)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k, v in host.items():
+            for c, t in enumerate(v):
+                p.field(k)[c].copy_(t, non_blocking=True)
+        bench_step()
+        for k, v in host.items():
+            for c, t in enumerate(v):
+                t.copy_(p.field(k)[c], non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_el = time.perf_counter() - t0
+    e2e_units, e2e_max = aggregate(n * RK2_PER_STEP * e2e_steps, e2e_el, dev)
+
+    rows = {} if args.no_rows else secondary_rows(sx, torch, p, d, dev)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = measured_peaks()
+    step_avg_s = statistics.mean(step_ms) / 1e3
+    achieved = BYTES_PER_PARTICLE_STEP * n / step_avg_s / 1e9
+    sort_launches = 1 + 3 * 2 + 1  # keys, (upsweep, scan, downsweep) x 2 passes, permute
+    line = {
+        "metric": METRIC, "value": tot_units / max_el, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sorted_n16M", "n": n, "fields": "i32 id, f64 pos[3], f32 vel[3]",
+                   "rk2_steps_per_step": RK2_PER_STEP, "grid": WL["grid"], "flow": "ABC A=B=C=1 tau=0.1 dt=1e-3",
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 ({n * 40 / 2**20:.0f} MiB of planes > 126 MiB)"},
+        "roofline": {"bound": "hbm", "kernel": "k_step_soa", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "bytes_per_unit": BYTES_PER_PARTICLE_STEP, "units_per_launch": n,
+                     "traffic": ncu_traffic("k_step_soa"), "launch_ms": statistics.mean(step_ms)},
+        "sort_ms": statistics.mean(sort_ms),
+        "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": h2d, "steps": e2e_steps},
+        "gpu_launches": args.steps * (RK2_PER_STEP + sort_launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu_baseline(n) if world == 1 or rank == 0 else None,
+        "rows": rows,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _time(torch, fn, reps=1):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def secondary_rows(sx, torch, p, d, dev):
+    rows = {}
+    n = p.n
+    flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
+    # AoS <-> SoA round trip (176 algorithmic bytes per particle) and the AoS step (96).
+    aos = p.to_aos()
+    t_rt = _time(torch, lambda: (p.to_aos(aos), p.from_aos(aos)), reps=5)
+    rows["aos_soa_roundtrip"] = {"ms": t_rt * 1e3, "GB/s": 176 * n / t_rt / 1e9, "bytes_per_particle": 176}
+    t_aos = _time(torch, lambda: p.step_aos(aos, flow, 1), reps=3)
+    t_soa = _time(torch, lambda: p.step(flow, 1), reps=3)
+    rows["aos_step"] = {"particle-steps/s": n / t_aos, "algorithmic_GB/s": 72 * n / t_aos / 1e9,
+                        "record_GB/s": 96 * n / t_aos / 1e9, "soa_over_aos": t_aos / t_soa}
+    del aos
+    torch.cuda.empty_cache()
+    # Forward + adjoint (1M particles, K = 1000, checkpoint every 32) vs the plain step.
+    wa = soax_inputs.WORKLOADS["adjoint_n1M"]
+    da = soax_inputs.basic_set(wa["n"], wa["seed"])
+    pa = sx.Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], wa["n"], device=dev, shadow=False)
+    fa = sx.Flow(A=wa["A"], B=wa["B"], C=wa["C"], tau=wa["tau"], dt=wa["dt"])
+    K, C = wa["K"], wa["ckpt_every"]
+    wsa = pa.adjoint_workspace(K, C)
+    xt = [torch.from_numpy(a).to(dev) for a in da["pos"]]
+
+    def reset():
+        pa.load({"pos": da["pos"], "vel": da["vel"]})
+
+    reset()
+    t_plain = _time(torch, lambda: pa.step(fa, K))
+    reset()
+
+    def fwd_adj():
+        pa.step_checkpointed(fa, K, C, wsa)
+        _, xb = pa.minimage_loss(xt, wsa)
+        pa.step_adjoint(fa, K, C, wsa, xb)
+    t_fa = _time(torch, fwd_adj)
+    rows["fwd_adjoint"] = {"n": wa["n"], "K": K, "ckpt_every": C, "plain_ms": t_plain * 1e3, "fwd_adj_ms": t_fa * 1e3,
+                           "ratio_vs_plain": t_fa / t_plain}
+    del pa, wsa, xt
+    torch.cuda.empty_cache()
+    # Batched: 512 uneven ensembles, a few steps, vs 512 plain launches per step.
+    wb = soax_inputs.WORKLOADS["batched_512"]
+    sizes, taus, abc = soax_inputs.ensembles(wb["nens"], wb["nmin"], wb["nmax"], wb["seed"])
+    parts, flows = [], []
+    for e, (ne, tau) in enumerate(zip(sizes, taus)):
+        q = sx.Particles(sx.BASIC_SCHEMA, int(ne), device=dev, shadow=False)
+        rng = np.random.default_rng(1000 + e)
+        pos = np.minimum(rng.uniform(0.0, soax_inputs.TWO_PI, (3, int(ne))), np.nextafter(soax_inputs.TWO_PI, 0))
+        vel = rng.normal(0.0, 0.1, (3, int(ne))).astype(np.float32)
+        q.load({"pos": list(pos), "vel": list(vel)})
+        parts.append(q)
+        flows.append(sx.Flow(A=abc[e, 0], B=abc[e, 1], C=abc[e, 2], tau=float(tau), dt=wb["dt"]))
+    total = int(sizes.sum())
+    nst = 5
+    tune = sx.autotune(parts, flows, nsteps_probe=1)
+    wsb = sx.step_batched(parts, flows, 1, tune)
+    t_b = _time(torch, lambda: sx.step_batched(parts, flows, nst, tune, ws=wsb))
+    tf = sx.Tune(tune.parts_per_thread, tune.block, tune.vec_bits, 1)
+    sx.step_batched(parts, flows, 1, tf, ws=wsb)
+    t_f = _time(torch, lambda: sx.step_batched(parts, flows, nst, tf, ws=wsb))
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            for q, f in zip(parts, flows):
+                q.step(f, 1, stream=s)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    t_plain_b = _time(torch, lambda: [g.replay() for _ in range(nst)])
+    rows["batched"] = {"ensembles": len(parts), "particles": total, "steps": nst,
+                       "tune": tune.__dict__,
+                       "persistent_particle-steps/s": total * nst / t_b,
+                       "fused_particle-steps/s": total * nst / t_f,
+                       "plain_512_launches_particle-steps/s": total * nst / t_plain_b,
+                       "persistent_over_plain": t_plain_b / t_b}
+    del parts, g
+    torch.cuda.empty_cache()
+    return rows
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_soax(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * soax.h -- C ABI of libsoax, a B300 (sm_103a) library for heterogeneous particle
+ * records stored as a Structure of Arrays (SoA).
+ *
+ * The container follows the paper's SoAx (Sec. 4): a particle type is a list of
+ * attributes, each an N-dimensional array of one scalar type with a one-character tag
+ * (SOAX_ATTRIBUTE(name, 'C') and the attribute tuple of Listing 5); the SoA holds one
+ * device array ("plane") per attribute component (posArr(d) in Listing 5).  Here the
+ * schema is a runtime value instead of a C++ type.
+ *
+ * Conventions for every call:
+ *  - Return value: SOAX_OK (0) or a negative soax_status.  No exception or abort crosses
+ *    this boundary.  soax_last_error() gives a message for the calling thread.
+ *  - Host-side validation (null pointers, schema, alignment, sizes) happens before any
+ *    launch; a failed validation launches nothing and changes nothing.
+ *  - Ownership: the library owns only the host-side handle.  Particle planes, shadow
+ *    planes, AoS buffers, keys, permutations and workspaces are device memory owned by
+ *    the caller (e.g. PyTorch tensors), and must stay valid while work that uses them is
+ *    in flight.  No call allocates device memory.
+ *  - Streams: every compute call is asynchronous on the given cudaStream_t (passed as
+ *    void*; NULL = the legacy default stream) on the calling thread's current device.
+ *    Calls do not synchronise with the host, except soax_sync(), soax_autotune() and
+ *    the first soax_step_batched() call for a new plan (documented there).
+ *  - Device-side errors set a per-device status word that soax_sync() reports and
+ *    clears.
+ *  - Plane layout: plane (f, c) of field f holds component c of every particle,
+ *    contiguous, element i at byte offset i*elem_size.  Every plane and AoS buffer must
+ *    be 16-byte aligned (SOAX_EALIGN otherwise).
+ */
+#ifndef SOAX_H
+#define SOAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SOAX_OK = 0,
+  SOAX_EINVAL = -1,       /* bad argument (null pointer, negative size, bad index)  */
+  SOAX_ESCHEMA = -2,      /* schema is malformed or lacks a field the call needs      */
+  SOAX_EALIGN = -3,       /* a device pointer is not 16-byte aligned                  */
+  SOAX_ECUDA = -4,        /* a CUDA runtime call or kernel launch failed              */
+  SOAX_ETIMEOUT = -5,     /* a bounded device-side wait gave up (see soax_sync)       */
+  SOAX_ENOMEM = -6,       /* the caller's workspace is smaller than required          */
+  SOAX_EUNSUPPORTED = -7, /* valid request this build does not implement              */
+  SOAX_EUNBOUND = -8      /* a plane the call needs has not been bound                */
+} soax_status;
+
+/* Scalar types of an attribute (Sec. 4.1: id<int,1>, pos<double,3>, mass<float,1>). */
+typedef enum { SOAX_I32 = 0, SOAX_I64 = 1, SOAX_U8 = 2, SOAX_F32 = 3, SOAX_F64 = 4 } soax_dtype;
+
+/* One attribute: SOAX_ATTRIBUTE(name, tag) with type<dtype, ncomp> (Listing 5).
+ * name: NUL-terminated, 1..31 chars, unique in the schema (copied at create).
+ * ncomp: 1..16.  tag: free descriptive character; soax_sort_by_cell uses the field
+ * tagged 'P' (f64 x 3) as the position. */
+typedef struct {
+  const char* name;
+  int32_t dtype;
+  int32_t ncomp;
+  char tag;
+} soax_field_desc;
+
+typedef struct soax_s* soax_t;
+
+/* Parameters of the inertial-particle step in the ABC flow
+ *   u(x,y,z) = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x),
+ *   dx/dt = v, dv/dt = (u(x) - v)/tau,
+ * integrated by the explicit midpoint rule with time step dt on the periodic box
+ * [0, 2pi)^3.  This generalises the paper's Euler advection x += dt*v (Eq. 1, Sec. 2). */
+typedef struct {
+  double A, B, C;    /* flow amplitudes (finite)                                   */
+  double tau;        /* uniform response time, used when tau_field < 0 (> 0)       */
+  double dt;         /* time step (> 0)                                            */
+  double tau_scale;  /* tau_i = tau_scale * (double)field[tau_field][i]            */
+  int32_t tau_field; /* index of an f32 x 1 field (e.g. mass), or -1                */
+  int32_t pos_field; /* index of the f64 x 3 position field                        */
+  int32_t vel_field; /* index of the f32 x 3 velocity field                        */
+  int32_t acc_field; /* index of an f32 x 3 field that receives the last stage
+                        acceleration of the last step, or -1                        */
+} soax_flow;
+
+/* Launch shape of the batched step.  parts_per_thread: 1, 2 or 4 particles per thread;
+ * block: 64..512, a multiple of 32; vec_bits: 64 or 128 (width of each plane load);
+ * fuse_steps: 0 = one pass over memory per step, 1 = all nsteps in registers. */
+typedef struct {
+  int32_t parts_per_thread;
+  int32_t block;
+  int32_t vec_bits;
+  int32_t fuse_steps;
+} soax_tune;
+
+/* ------------------------------------------------------------------ handles */
+
+/* Library ABI version (currently 1). */
+int soax_version(void);
+
+/* Message for the last failed call on this thread ("" if none).  The pointer stays
+ * valid until the next call on this thread. */
+const char* soax_last_error(void);
+
+/* Build a handle for n particles (0 <= n < 2^31) with the given schema
+ * (Listing 5: Soax<ArrayTypes> soax(42)).  Host only; allocates no device memory.
+ * SOAX_ESCHEMA on a malformed schema (bad dtype, ncomp out of range, duplicate or empty
+ * name, more than 32 fields or 64 planes). */
+int soax_create(const soax_field_desc* fields, int32_t nfields, int64_t n, soax_t* out);
+
+/* Release a handle (host memory only; bound planes are not freed).  NULL is accepted. */
+int soax_destroy(soax_t h);
+
+/* Number of particles, fields, and planes of a handle (any output may be NULL). */
+int soax_size(soax_t h, int64_t* n, int32_t* nfields, int32_t* nplanes);
+
+/* Attach caller-owned device memory to plane (field, comp) of buffer set buf
+ * (0 = primary, 1 = shadow used as the destination of soax_sort_by_cell).  dev_ptr
+ * must hold n elements of the field's type and be 16-byte aligned (SOAX_EALIGN). */
+int soax_bind(soax_t h, int32_t field, int32_t comp, int32_t buf, void* dev_ptr);
+
+/* Which buffer set (0 or 1) currently holds the particles.  soax_sort_by_cell and
+ * soax_permute flip it; soax_set_current sets it. */
+int soax_current(soax_t h, int32_t* buf);
+int soax_set_current(soax_t h, int32_t buf);
+
+/* Natural C layout of the AoS record of this schema (the structs of Listing 1 and 4):
+ * fields in schema order, each at the next multiple of its scalar size, the size rounded
+ * up to the largest scalar size.  field_offsets receives nfields values (may be NULL). */
+int soax_aos_layout(soax_t h, int64_t* record_bytes, int64_t* field_offsets);
+
+/* ------------------------------------------------------------- transposes */
+
+/* Bulk getElement (Listing 6, Sec. 4.1): copy n AoS records (layout from
+ * soax_aos_layout, 16-byte aligned device buffer) into the live planes, byte for byte;
+ * padding bytes are ignored. */
+int soax_aos_to_soa(soax_t h, const void* aos_dev, void* stream);
+
+/* Bulk push_back (Listing 6): copy the live planes into n AoS records, byte for byte,
+ * padding bytes written as 0. */
+int soax_soa_to_aos(soax_t h, void* aos_dev, void* stream);
+
+/* -------------------------------------------------------------------- step */
+
+/* Advance every particle nsteps (>= 0) midpoint-RK2 steps in place on the live planes:
+ *   a1 = (u(x) - v)/tau,  xm = x + dt/2 v,  vm = v + dt/2 a1,  a2 = (u(xm) - vm)/tau,
+ *   x' = x + dt vm (wrapped once into [0, 2pi)),  v' = v + dt a2 rounded to f32,
+ * with f64-accurate arithmetic (v is promoted from f32).  One pass over the planes per
+ * step; each step is one kernel launch (capturable in a CUDA graph). */
+int soax_step(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream);
+
+/* The same step, bit-identical per particle, on AoS records in place (layout from
+ * soax_aos_layout; the flow's field indices refer to this handle's schema). */
+int soax_step_aos(soax_t h, void* aos_dev, const soax_flow* fl, int32_t nsteps, void* stream);
+
+/* ------------------------------------------------------------- cell sort */
+
+/* keys[i] = (iz*G + iy)*G + ix of the live position field pos_field, with
+ * i_d = min((int)(x_d * (G/2pi)), G-1) computed in binary64 (G/2pi rounded once).
+ * grid G in 1..1024; keys: n u32, 16-byte aligned. */
+int soax_cell_keys(soax_t h, int32_t pos_field, int32_t grid, uint32_t* keys, void* stream);
+
+/* Workspace bytes soax_radix_sort_pairs needs for n keys of key_bits significant bits. */
+int soax_radix_workspace_bytes(int64_t n, int32_t key_bits, size_t* bytes);
+
+/* Stable ascending LSD radix sort of (key, value) pairs by the low key_bits (1..32) bits
+ * of key.  vals_in may be NULL (then value i = i, i.e. vals_out is the stable argsort).
+ * keys_out may be NULL (sorted keys not wanted).  Inputs are not modified; outputs must
+ * not alias inputs.  All arrays hold n u32 and are 16-byte aligned; ws holds
+ * soax_radix_workspace_bytes bytes. */
+int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                          uint32_t* vals_out, int64_t n, int32_t key_bits, void* ws,
+                          size_t ws_bytes, void* stream);
+
+/* out_f[i] = in_f[perm[i]] for every plane of every field, from the live buffer set to
+ * the other one (apply-to-all-arrays, Listing 7), then flip the live set.  perm must be
+ * a permutation of 0..n-1 (not checked). */
+int soax_permute(soax_t h, const uint32_t* perm, void* stream);
+
+/* Workspace bytes soax_sort_by_cell needs. */
+int soax_sort_workspace_bytes(soax_t h, int32_t grid, size_t* bytes);
+
+/* Cell keys of the field tagged 'P' on a grid^3 grid, stable radix sort, permute-gather
+ * of all fields into the shadow set, flip.  The sorted keys and the permutation are left
+ * in the workspace (soax_sort_results gives their addresses). */
+int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_bytes, void* stream);
+int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
+                      uint32_t** perm);
+
+/* ---------------------------------------------------------------- adjoint */
+
+/* Workspace bytes for K steps with a checkpoint every ckpt_every steps. */
+int soax_adjoint_workspace_bytes(soax_t h, int32_t K, int32_t ckpt_every, size_t* bytes);
+
+/* Forward: K steps in place (bit-identical to soax_step), saving the state at steps
+ * 0, ckpt_every, 2*ckpt_every, ... into ws.  tau_field must be -1. */
+int soax_step_checkpointed(soax_t h, const soax_flow* fl, int32_t K, int32_t ckpt_every, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/* Reverse: given adjoints xbarK (3 f64 planes) and vbarK (3 f64 planes, or NULL for 0)
+ * of the state after the K steps of the last soax_step_checkpointed on this ws,
+ * recompute each segment from its checkpoint and write xbar0, vbar0 (3 f64 planes each)
+ * and grad[4] = dL/d(A, B, C, tau) (device f64[4], summed over particles in a fixed
+ * order: the result is bit-reproducible).  The f32 rounding of v and the periodic wrap
+ * are differentiated as the identity.  Pointer arrays are host arrays of 3 device
+ * pointers. */
+int soax_step_adjoint(soax_t h, const soax_flow* fl, int32_t K, int32_t ckpt_every, void* ws,
+                      size_t ws_bytes, const double* const* xbarK, const double* const* vbarK,
+                      double* const* xbar0, double* const* vbar0, double* grad, void* stream);
+
+/* L = (1/n) sum_p |d_p|^2 with d the minimum image of x_p - xtgt_p in the periodic box,
+ * written to loss (device f64[1]); if xbar is not NULL, xbar = dL/dx = (2/n) d (3 f64
+ * planes).  Deterministic.  xtgt: host array of 3 device pointers.  ws: at least
+ * 8*ceil(n/256) bytes (an adjoint workspace of the same handle always suffices). */
+int soax_minimage_loss(soax_t h, int32_t pos_field, const double* const* xtgt, double* loss,
+                       double* const* xbar, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- batched */
+
+/* Workspace bytes for advancing nens ensembles with soax_step_batched (any tune). */
+int soax_batched_workspace_bytes(const soax_t* hs, int32_t nens, const soax_tune* tune,
+                                 size_t* bytes);
+
+/* Advance nens (1..4096) independent ensembles (each its own handle and soax_flow; dt
+ * must be equal) nsteps steps, every step one persistent launch over all ensembles (or,
+ * with tune->fuse_steps, one launch for all steps).  Per particle the arithmetic is
+ * bit-identical to soax_step.  The first call for a given (hs, fls, tune, ws) builds a
+ * tile table on the host and copies it into ws, synchronising the stream; later calls
+ * with the same arguments only launch, so they can be captured in a CUDA graph.
+ * tune == NULL: parts_per_thread 4, block 256, vec_bits 128, no fusion. */
+int soax_step_batched(const soax_t* hs, const soax_flow* fls, int32_t nens, int32_t nsteps,
+                      const soax_tune* tune, void* ws, size_t ws_bytes, void* stream);
+
+/* Time every candidate launch shape on nsteps_probe steps of the given ensembles (which
+ * it advances: pass scratch copies) and write the fastest to out.  Synchronises. */
+int soax_autotune(const soax_t* hs, const soax_flow* fls, int32_t nens, int32_t nsteps_probe,
+                  void* ws, size_t ws_bytes, soax_tune* out, void* stream);
+
+/* ------------------------------------------------------------------ status */
+
+/* Synchronise stream, then report and clear the device status word of the current
+ * device: SOAX_OK, or the code a device-side check stored since the last soax_sync.
+ * SOAX_ECUDA if the stream reported an error. */
+int soax_sync(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOAX_H */

@@ -1,0 +1,394 @@
+"""soax-b300: a Structure-of-Arrays particle container for the NVIDIA B300 (sm_103a).
+
+Python binding of the C-ABI library libsoax.so (include/soax.h).  This module only
+marshals arguments: every step of the computation runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.
+
+The container follows the paper's SoAx (Sec. 4): a particle type is a list of
+attributes (name, scalar type, number of components, one-character tag), stored as one
+device array per component.  On top of it the library runs
+
+  * the inertial-particle midpoint-RK2 step in the ABC flow (soax_step), generalising
+    the Euler advection x += dt*v of Eq. 1 (Sec. 2), on SoA planes or AoS records;
+  * the cell-key radix sort and the permute-gather of every plane (soax_sort_by_cell);
+  * the AoS <-> SoA transposes (bulk getElement / push_back of Listing 6);
+  * the checkpointed forward and its adjoint (SoaxRK2, a torch.autograd.Function);
+  * a batched persistent step over many ensembles, with an autotuner.
+
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+import ctypes as C
+import hashlib
+import json
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _abi
+from ._abi import DTYPES, STATUS_NAMES, soax_field_desc, soax_flow, soax_tune
+
+__all__ = ["SoaxError", "lib", "Particles", "Flow", "Tune", "radix_sort_pairs", "step_batched",
+           "batched_workspace", "autotune", "sync", "SoaxRK2", "TWO_PI", "BASIC_SCHEMA", "WIDE_SCHEMA"]
+
+TWO_PI = 6.283185307179586
+
+# The record of the program summary, {int id; double pos[3]; float vel[3];}, with the
+# tags of Listing 5 (N identity, P position, V velocity).
+BASIC_SCHEMA = [("id", "i32", 1, "N"), ("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")]
+# A wider heterogeneous record (acceleration, mass, a small integer tag).
+WIDE_SCHEMA = [("id", "i64", 1, "N"), ("pos", "f64", 3, "P"), ("vel", "f32", 3, "V"),
+               ("acc", "f32", 3, "A"), ("mass", "f32", 1, "M"), ("tag", "u8", 1, "T")]
+
+TORCH_DTYPES = {"i32": torch.int32, "i64": torch.int64, "u8": torch.uint8, "f32": torch.float32,
+                "f64": torch.float64}
+
+
+class SoaxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def lib():
+    """Load libsoax.so (building it in-tree with nvcc if it is missing)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_abi.LIB_PATH):
+            from . import build as _build
+            _build.build()
+        _LIB = _abi.declare(C.CDLL(_abi.LIB_PATH))
+    return _LIB
+
+
+def _check(rc, what=""):
+    if rc != 0:
+        msg = lib().soax_last_error().decode(errors="replace")
+        raise SoaxError(rc, f"{what}: {msg}" if what else msg)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _ptr3(ts):
+    if ts is None:
+        return None
+    return (C.c_void_p * 3)(*[t.data_ptr() for t in ts])
+
+
+def sync(stream=None):
+    """Synchronise the stream and report a device-side error as SoaxError."""
+    _check(lib().soax_sync(_stream(stream)), "soax_sync")
+
+
+@dataclass
+class Flow:
+    """Parameters of the inertial-particle step (include/soax.h: soax_flow)."""
+    A: float = 1.0
+    B: float = 1.0
+    C: float = 1.0
+    tau: float = 0.1
+    dt: float = 1e-3
+    tau_field: str = None   # name of an f32 x 1 field; tau_i = tau_scale * field[i]
+    tau_scale: float = 0.0
+    pos: str = "pos"
+    vel: str = "vel"
+    acc: str = None
+
+
+@dataclass
+class Tune:
+    parts_per_thread: int = 4
+    block: int = 256
+    vec_bits: int = 128
+    fuse_steps: int = 0
+
+    def c(self):
+        return soax_tune(self.parts_per_thread, self.block, self.vec_bits, self.fuse_steps)
+
+
+class Particles:
+    """n particles of a schema, one torch tensor per (field, component) and buffer set.
+
+    schema: list of (name, dtype in {'i32','i64','u8','f32','f64'}, ncomp, tag).
+    shadow: also allocate the second buffer set (needed by sort_by_cell / permute).
+    """
+
+    def __init__(self, schema, n, device=None, shadow=True):
+        self.schema = [(str(a), str(b), int(c), str(d)) for a, b, c, d in schema]
+        self.n = int(n)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._names = [s[0] for s in self.schema]
+        descs = (soax_field_desc * len(self.schema))()
+        self._keep = []
+        for k, (name, dt, nc, tag) in enumerate(self.schema):
+            b = name.encode()
+            self._keep.append(b)
+            descs[k] = soax_field_desc(b, DTYPES[dt], nc, tag.encode()[:1])
+        h = C.c_void_p()
+        _check(lib().soax_create(descs, len(self.schema), self.n, C.byref(h)), "soax_create")
+        self.h = h
+        self.planes = [{}, {}]
+        for buf in (0, 1) if shadow else (0,):
+            for k, (name, dt, nc, _) in enumerate(self.schema):
+                ts = [torch.empty(self.n, dtype=TORCH_DTYPES[dt], device=self.device) for _ in range(nc)]
+                for c, t in enumerate(ts):
+                    _check(lib().soax_bind(self.h, k, c, buf, _ptr(t) if self.n else None), "soax_bind")
+                self.planes[buf][name] = ts
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _LIB is not None:
+            _LIB.soax_destroy(h)
+            self.h = None
+
+    # ------------------------------------------------------------------ fields
+    def fidx(self, name):
+        return self._names.index(name)
+
+    @property
+    def current(self):
+        b = C.c_int32()
+        _check(lib().soax_current(self.h, C.byref(b)))
+        return b.value
+
+    def set_current(self, buf):
+        _check(lib().soax_set_current(self.h, int(buf)))
+
+    def field(self, name, buf=None):
+        """The component tensors of a field in the live (or given) buffer set."""
+        return self.planes[self.current if buf is None else buf][name]
+
+    def load(self, arrays):
+        """Copy host or device arrays into the live planes: {name: [comp0, comp1, ...]}."""
+        for name, comps in arrays.items():
+            dst = self.field(name)
+            for c, a in enumerate(comps):
+                dst[c].copy_(torch.as_tensor(a))
+
+    def numpy(self):
+        """Live planes as numpy arrays (synchronises)."""
+        return {name: [t.cpu().numpy() for t in self.field(name)] for name in self._names}
+
+    def flow(self, f: Flow):
+        return soax_flow(f.A, f.B, f.C, f.tau, f.dt, f.tau_scale,
+                         self.fidx(f.tau_field) if f.tau_field else -1, self.fidx(f.pos), self.fidx(f.vel),
+                         self.fidx(f.acc) if f.acc else -1)
+
+    # ------------------------------------------------------------------ ops
+    def step(self, f: Flow, nsteps=1, stream=None):
+        fl = self.flow(f)
+        _check(lib().soax_step(self.h, C.byref(fl), int(nsteps), _stream(stream)), "soax_step")
+
+    def aos_layout(self):
+        rb = C.c_int64()
+        offs = (C.c_int64 * len(self.schema))()
+        _check(lib().soax_aos_layout(self.h, C.byref(rb), offs))
+        return rb.value, list(offs)
+
+    def new_aos(self):
+        rb, _ = self.aos_layout()
+        return torch.empty(self.n * rb, dtype=torch.uint8, device=self.device)
+
+    def to_aos(self, out=None, stream=None):
+        out = self.new_aos() if out is None else out
+        _check(lib().soax_soa_to_aos(self.h, _ptr(out), _stream(stream)), "soax_soa_to_aos")
+        return out
+
+    def from_aos(self, aos, stream=None):
+        _check(lib().soax_aos_to_soa(self.h, _ptr(aos), _stream(stream)), "soax_aos_to_soa")
+
+    def step_aos(self, aos, f: Flow, nsteps=1, stream=None):
+        fl = self.flow(f)
+        _check(lib().soax_step_aos(self.h, _ptr(aos), C.byref(fl), int(nsteps), _stream(stream)), "soax_step_aos")
+
+    def cell_keys(self, grid, pos="pos", out=None, stream=None):
+        out = torch.empty(self.n, dtype=torch.int32, device=self.device) if out is None else out
+        _check(lib().soax_cell_keys(self.h, self.fidx(pos), int(grid), _ptr(out), _stream(stream)), "soax_cell_keys")
+        return out
+
+    def sort_workspace(self, grid):
+        b = C.c_size_t()
+        _check(lib().soax_sort_workspace_bytes(self.h, int(grid), C.byref(b)))
+        return torch.empty(max(b.value, 16), dtype=torch.uint8, device=self.device)
+
+    def sort_by_cell(self, grid, ws=None, stream=None):
+        """Cell sort of every field; returns (sorted keys, perm) as int32 views into ws."""
+        ws = self.sort_workspace(grid) if ws is None else ws
+        _check(lib().soax_sort_by_cell(self.h, int(grid), _ptr(ws), ws.numel(), _stream(stream)), "soax_sort_by_cell")
+        return self.sort_results(grid, ws)
+
+    def sort_results(self, grid, ws):
+        k, p = C.c_void_p(), C.c_void_p()
+        _check(lib().soax_sort_results(self.h, int(grid), _ptr(ws), ws.numel(), C.byref(k), C.byref(p)))
+        base = ws.data_ptr()
+        ko, po = (k.value or base) - base, (p.value or base) - base
+        kt = ws[ko:ko + 4 * self.n].view(torch.int32)
+        pt = ws[po:po + 4 * self.n].view(torch.int32)
+        return kt, pt
+
+    def permute(self, perm, stream=None):
+        _check(lib().soax_permute(self.h, _ptr(perm), _stream(stream)), "soax_permute")
+
+    # ------------------------------------------------------------------ adjoint
+    def adjoint_workspace(self, K, ckpt_every):
+        b = C.c_size_t()
+        _check(lib().soax_adjoint_workspace_bytes(self.h, int(K), int(ckpt_every), C.byref(b)))
+        return torch.empty(max(b.value, 16), dtype=torch.uint8, device=self.device)
+
+    def step_checkpointed(self, f: Flow, K, ckpt_every, ws, stream=None):
+        fl = self.flow(f)
+        _check(lib().soax_step_checkpointed(self.h, C.byref(fl), int(K), int(ckpt_every), _ptr(ws), ws.numel(),
+                                            _stream(stream)), "soax_step_checkpointed")
+
+    def step_adjoint(self, f: Flow, K, ckpt_every, ws, xbarK, vbarK=None, stream=None):
+        """Returns (xbar0 [3], vbar0 [3], grad[A, B, C, tau]) as f64 tensors."""
+        fl = self.flow(f)
+        xb0 = [torch.empty(self.n, dtype=torch.float64, device=self.device) for _ in range(3)]
+        vb0 = [torch.empty(self.n, dtype=torch.float64, device=self.device) for _ in range(3)]
+        grad = torch.empty(4, dtype=torch.float64, device=self.device)
+        xk = [t.contiguous() for t in xbarK]
+        vk = [t.contiguous() for t in vbarK] if vbarK is not None else None
+        _check(lib().soax_step_adjoint(self.h, C.byref(fl), int(K), int(ckpt_every), _ptr(ws), ws.numel(),
+                                       _ptr3(xk), _ptr3(vk), _ptr3(xb0), _ptr3(vb0), _ptr(grad), _stream(stream)),
+               "soax_step_adjoint")
+        return xb0, vb0, grad
+
+    def minimage_loss(self, xtgt, ws, want_grad=True, pos="pos", stream=None):
+        loss = torch.empty(1, dtype=torch.float64, device=self.device)
+        xb = [torch.empty(self.n, dtype=torch.float64, device=self.device) for _ in range(3)] if want_grad else None
+        xt = [t.contiguous() for t in xtgt]
+        _check(lib().soax_minimage_loss(self.h, self.fidx(pos), _ptr3(xt), _ptr(loss), _ptr3(xb), _ptr(ws),
+                                        ws.numel(), _stream(stream)), "soax_minimage_loss")
+        return loss, xb
+
+
+def radix_sort_pairs(keys, vals=None, key_bits=32, want_keys=True, ws=None, stream=None):
+    """Stable LSD radix sort of (u32 key, u32 value); vals None = argsort.  Tensors are
+    int32 holding the u32 bit patterns.  Returns (sorted keys or None, sorted values)."""
+    n = keys.numel()
+    b = C.c_size_t()
+    _check(lib().soax_radix_workspace_bytes(n, int(key_bits), C.byref(b)))
+    ws = torch.empty(max(b.value, 16), dtype=torch.uint8, device=keys.device) if ws is None else ws
+    ko = torch.empty_like(keys) if want_keys else None
+    vo = torch.empty(n, dtype=torch.int32, device=keys.device)
+    _check(lib().soax_radix_sort_pairs(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), n, int(key_bits), _ptr(ws),
+                                       ws.numel(), _stream(stream)), "soax_radix_sort_pairs")
+    return ko, vo
+
+
+def _handles(parts):
+    return (C.c_void_p * len(parts))(*[p.h.value for p in parts])
+
+
+def _flows(parts, flows):
+    arr = (soax_flow * len(parts))()
+    for k, (p, f) in enumerate(zip(parts, flows)):
+        arr[k] = p.flow(f)
+    return arr
+
+
+def batched_workspace(parts):
+    b = C.c_size_t()
+    _check(lib().soax_batched_workspace_bytes(_handles(parts), len(parts), None, C.byref(b)))
+    return torch.empty(max(b.value, 16), dtype=torch.uint8, device=parts[0].device)
+
+
+def step_batched(parts, flows, nsteps, tune: Tune = None, ws=None, stream=None):
+    """Advance every ensemble nsteps steps, one persistent launch per step (or one in
+    total with tune.fuse_steps).  The first call for a new (ensembles, tune, ws) uploads a
+    tile plan and synchronises; later identical calls only launch."""
+    ws = batched_workspace(parts) if ws is None else ws
+    t = tune.c() if tune is not None else None
+    _check(lib().soax_step_batched(_handles(parts), _flows(parts, flows), len(parts), int(nsteps),
+                                   C.byref(t) if t is not None else None, _ptr(ws), ws.numel(), _stream(stream)),
+           "soax_step_batched")
+    return ws
+
+
+def _tune_cache_path():
+    return os.path.join(os.path.expanduser("~"), ".cache", "soax_b300", "autotune.json")
+
+
+def _tune_key(parts):
+    schema = json.dumps(parts[0].schema)
+    total = sum(p.n for p in parts)
+    gpu = torch.cuda.get_device_name(parts[0].device)
+    return f"{gpu}|{hashlib.sha1(schema.encode()).hexdigest()[:12]}|n2^{total.bit_length()}|e{len(parts)}"
+
+
+def autotune(parts, flows, nsteps_probe=2, use_cache=True, stream=None):
+    """Pick the fastest launch shape for step_batched on these ensembles.  Times every
+    candidate on scratch copies (the ensembles are not modified) and caches the result
+    in ~/.cache/soax_b300/autotune.json keyed by (GPU, schema, size bucket, #ensembles)."""
+    key = _tune_key(parts)
+    path = _tune_cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as fh:
+                cache = json.load(fh)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            return Tune(**cache[key])
+    scratch = []
+    for p in parts:
+        q = Particles(p.schema, p.n, device=p.device, shadow=False)
+        for name in p._names:
+            for c, t in enumerate(p.field(name)):
+                q.planes[0][name][c].copy_(t)
+        scratch.append(q)
+    ws = batched_workspace(scratch)
+    out = soax_tune()
+    _check(lib().soax_autotune(_handles(scratch), _flows(scratch, flows), len(scratch), int(nsteps_probe), _ptr(ws),
+                               ws.numel(), C.byref(out), _stream(stream)), "soax_autotune")
+    t = Tune(out.parts_per_thread, out.block, out.vec_bits, out.fuse_steps)
+    if use_cache:
+        cache[key] = t.__dict__
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as fh:
+                json.dump(cache, fh, indent=1)
+        except OSError:
+            pass
+    return t
+
+
+class SoaxRK2(torch.autograd.Function):
+    """x_K = RK2^K(x0, v0; A, B, C, tau) with a hand-written adjoint.
+
+    forward(x0 [3, n] f64, v0 [3, n] (f32 values), theta [4] f64 = (A, B, C, tau), dt, K,
+    ckpt_every) -> x_K [3, n] f64.  The forward runs soax_step_checkpointed (state saved
+    every ckpt_every steps); backward runs soax_step_adjoint, which recomputes each
+    segment from its checkpoint.  Gradients flow to x0, v0 and theta."""
+
+    @staticmethod
+    def forward(ctx, x0, v0, theta, dt, K, ckpt_every):
+        n = x0.shape[1]
+        th = [float(t) for t in theta.detach().cpu().tolist()]
+        p = Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], n, device=x0.device, shadow=False)
+        for c in range(3):
+            p.planes[0]["pos"][c].copy_(x0[c])
+            p.planes[0]["vel"][c].copy_(v0[c])
+        f = Flow(A=th[0], B=th[1], C=th[2], tau=th[3], dt=float(dt))
+        ws = p.adjoint_workspace(int(K), int(ckpt_every))
+        p.step_checkpointed(f, int(K), int(ckpt_every), ws)
+        ctx.p, ctx.f, ctx.ws, ctx.K, ctx.C = p, f, ws, int(K), int(ckpt_every)
+        ctx.v_dtype = v0.dtype
+        return torch.stack([t.clone() for t in p.planes[0]["pos"]])
+
+    @staticmethod
+    def backward(ctx, gx):
+        gx = gx.to(torch.float64)
+        xb0, vb0, grad = ctx.p.step_adjoint(ctx.f, ctx.K, ctx.C, ctx.ws, [gx[c].contiguous() for c in range(3)])
+        return torch.stack(xb0), torch.stack(vb0).to(ctx.v_dtype), grad, None, None, None

@@ -1,0 +1,290 @@
+// Checkpointed forward and hand-written adjoint of the midpoint-RK2 step, and the
+// minimum-image loss that seeds it.
+//
+// Every particle is independent, so one thread owns one particle for the whole
+// computation.  The forward keeps the particle in registers for all K steps and writes
+// its state every C steps (checkpoint j = state before step j*C).  The reverse walks the
+// segments backwards: it recomputes a segment from its checkpoint, pushing the C
+// states on a per-particle stack in the workspace (coalesced [step][plane][particle]
+// layout), then applies the reverse step C times.  Parameter gradients are reduced in a
+// fixed order (per-block tree, then one block over the block partials), so the result
+// is bit-reproducible.
+#include "soax_internal.h"
+#include "step_core.cuh"
+
+namespace soax {
+
+constexpr int kAdjBlock = 128;
+constexpr int kLossBlock = 256;
+
+__host__ __device__ static inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct AdjWs {
+  size_t state_bytes, off_partials, off_ckpt, off_stack, total;
+  int nck;
+};
+
+static AdjWs adj_plan(int64_t n, int K, int C) {
+  AdjWs w;
+  w.state_bytes = a256((size_t)n * 24) + a256((size_t)n * 12);
+  w.nck = (K + C - 1) / C;
+  const size_t nb_adj = (size_t)((n + kAdjBlock - 1) / kAdjBlock);
+  const size_t nb_loss = (size_t)((n + kLossBlock - 1) / kLossBlock);
+  w.off_partials = 0;
+  w.off_ckpt = a256((nb_adj * 4 > nb_loss ? nb_adj * 4 : nb_loss) * 8 + 8);
+  w.off_stack = w.off_ckpt + (size_t)w.nck * w.state_bytes;
+  w.total = w.off_stack + (size_t)(K < C ? K : C) * w.state_bytes;
+  return w;
+}
+
+struct StateRef {
+  double* x[3];
+  float* v[3];
+};
+
+__device__ __forceinline__ StateRef state_at(char* base, size_t sb, int64_t n, int j) {
+  char* p = base + (size_t)j * sb;
+  StateRef r;
+  double* xs = reinterpret_cast<double*>(p);
+  float* vs = reinterpret_cast<float*>(p + a256((size_t)n * 24));
+  for (int c = 0; c < 3; ++c) {
+    r.x[c] = xs + (size_t)c * n;
+    r.v[c] = vs + (size_t)c * n;
+  }
+  return r;
+}
+
+__global__ void __launch_bounds__(kAdjBlock) k_adj_forward(EnsArgs e, FlowK f, int K, int C, char* ckpt, size_t sb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= e.n) return;
+  double x[3] = {e.px[i], e.py[i], e.pz[i]};
+  float v[3] = {e.vx[i], e.vy[i], e.vz[i]}, a[3] = {0.f, 0.f, 0.f};
+  for (int s = 0; s < K; ++s) {
+    if (s % C == 0) {
+      StateRef r = state_at(ckpt, sb, e.n, s / C);
+      for (int c = 0; c < 3; ++c) {
+        r.x[c][i] = x[c];
+        r.v[c][i] = v[c];
+      }
+    }
+    rk2_step(f, e.inv_tau, x, v, a);
+  }
+  e.px[i] = x[0]; e.py[i] = x[1]; e.pz[i] = x[2];
+  e.vx[i] = v[0]; e.vy[i] = v[1]; e.vz[i] = v[2];
+  if (e.ax && K > 0) { e.ax[i] = a[0]; e.ay[i] = a[1]; e.az[i] = a[2]; }
+}
+
+struct AdjIO {
+  const double* xbK[3];
+  const double* vbK[3];  // all null: zero
+  double* xb0[3];
+  double* vb0[3];
+};
+
+// Fixed-order block reduction of NV doubles per thread into out[0..NV) (thread 0).
+template <int NV, int BLOCK>
+__device__ __forceinline__ void block_reduce_fixed(double (&v)[NV], double* out) {
+  __shared__ double red[NV][BLOCK];
+  for (int k = 0; k < NV; ++k) red[k][threadIdx.x] = v[k];
+  __syncthreads();
+  for (int w = BLOCK / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < NV; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NV; ++k) out[k] = red[k][0];
+}
+
+__global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, int K, int C, int nck, char* ckpt,
+                                                          char* stack, size_t sb, AdjIO io, double* partials) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double th[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < e.n) {
+    double xb[3], vb[3];
+    for (int c = 0; c < 3; ++c) {
+      xb[c] = io.xbK[c][i];
+      vb[c] = io.vbK[0] ? io.vbK[c][i] : 0.0;
+    }
+    float a[3];
+    for (int seg = nck - 1; seg >= 0; --seg) {
+      const int s0 = seg * C, len = (K - s0 < C) ? K - s0 : C;
+      StateRef ck = state_at(ckpt, sb, e.n, seg);
+      double x[3];
+      float v[3];
+      for (int c = 0; c < 3; ++c) {
+        x[c] = ck.x[c][i];
+        v[c] = ck.v[c][i];
+      }
+      for (int j = 0; j < len; ++j) {
+        StateRef st = state_at(stack, sb, e.n, j);
+        for (int c = 0; c < 3; ++c) {
+          st.x[c][i] = x[c];
+          st.v[c][i] = v[c];
+        }
+        rk2_step(f, e.inv_tau, x, v, a);
+      }
+      for (int j = len - 1; j >= 0; --j) {
+        StateRef st = state_at(stack, sb, e.n, j);
+        for (int c = 0; c < 3; ++c) {
+          x[c] = st.x[c][i];
+          v[c] = st.v[c][i];
+        }
+        rk2_reverse_native(f, e.inv_tau, x, v, xb, vb, th);
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      io.xb0[c][i] = xb[c];
+      io.vb0[c][i] = vb[c];
+    }
+  }
+  block_reduce_fixed<4, kAdjBlock>(th, partials + 4 * (size_t)blockIdx.x);
+}
+
+// One block: out[k] = scale * sum over b of partials[b*width + k], in a fixed order.
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* partials, int64_t nblocks, int width,
+                                                         double scale, double* out) {
+  __shared__ double red[256];
+  for (int k = 0; k < width; ++k) {
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < nblocks; b += 256) s += partials[b * width + k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0] * scale;
+    __syncthreads();
+  }
+}
+
+struct LossIO {
+  const double* x[3];
+  const double* xt[3];
+  double* xb[3];  // null: not wanted
+};
+
+__global__ void __launch_bounds__(kLossBlock) k_minimage_loss(LossIO io, int64_t n, double two_over_n,
+                                                              double* partials) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double l[1] = {0.0};
+  if (i < n) {
+    const double half = 0.5 * SOAX_TWO_PI;
+    for (int c = 0; c < 3; ++c) {
+      double d = io.x[c][i] - io.xt[c][i];
+      if (d > half)
+        d -= SOAX_TWO_PI;
+      else if (d < -half)
+        d += SOAX_TWO_PI;
+      l[0] += d * d;
+      if (io.xb[0]) io.xb[c][i] = two_over_n * d;
+    }
+  }
+  block_reduce_fixed<1, kLossBlock>(l, partials + blockIdx.x);
+}
+
+static int check_ptrs3(const void* const* p, bool allow_null, const char* what) {
+  if (!p) return allow_null ? SOAX_OK : fail(SOAX_EINVAL, std::string(what) + " is NULL");
+  for (int c = 0; c < 3; ++c) {
+    if (!p[c]) return fail(SOAX_EINVAL, std::string(what) + ": NULL plane");
+    if (!aligned16(p[c])) return fail(SOAX_EALIGN, std::string(what) + ": plane not 16-byte aligned");
+  }
+  return SOAX_OK;
+}
+
+static int adj_common(soax_t h, const soax_flow* fl, int32_t K, int32_t C, void* ws, size_t ws_bytes, EnsArgs* e,
+                      FlowK* f, AdjWs* w, const char* who) {
+  if (int r = check_handle(h)) return r;
+  if (K < 0 || C < 1) return fail(SOAX_EINVAL, std::string(who) + ": K >= 0 and ckpt_every >= 1 required");
+  if (int r = make_ens_args(h, fl, h->current, e, f, who)) return r;
+  if (fl->tau_field >= 0) return fail(SOAX_EUNSUPPORTED, std::string(who) + ": per-particle tau is not differentiated");
+  *w = adj_plan(h->n, K, C);
+  if (h->n > 0 && (!ws || ws_bytes < w->total)) return fail(SOAX_ENOMEM, std::string(who) + ": workspace too small");
+  if (!aligned16(ws)) return fail(SOAX_EALIGN, std::string(who) + ": workspace not 16-byte aligned");
+  return SOAX_OK;
+}
+
+}  // namespace soax
+
+using namespace soax;
+
+extern "C" int soax_adjoint_workspace_bytes(soax_t h, int32_t K, int32_t ckpt_every, size_t* bytes) {
+  if (int r = check_handle(h)) return r;
+  if (!bytes || K < 0 || ckpt_every < 1) return fail(SOAX_EINVAL, "soax_adjoint_workspace_bytes: bad argument");
+  *bytes = adj_plan(h->n, K, ckpt_every).total;
+  return SOAX_OK;
+}
+
+extern "C" int soax_step_checkpointed(soax_t h, const soax_flow* fl, int32_t K, int32_t ckpt_every, void* ws,
+                                      size_t ws_bytes, void* stream) {
+  EnsArgs e;
+  FlowK f;
+  AdjWs w;
+  if (int r = adj_common(h, fl, K, ckpt_every, ws, ws_bytes, &e, &f, &w, "soax_step_checkpointed")) return r;
+  if (h->n == 0 || K == 0) return SOAX_OK;
+  k_adj_forward<<<grid_for(h->n, kAdjBlock), kAdjBlock, 0, as_stream(stream)>>>(
+      e, f, K, ckpt_every, static_cast<char*>(ws) + w.off_ckpt, w.state_bytes);
+  return check_launch("soax_step_checkpointed");
+}
+
+extern "C" int soax_step_adjoint(soax_t h, const soax_flow* fl, int32_t K, int32_t ckpt_every, void* ws,
+                                 size_t ws_bytes, const double* const* xbarK, const double* const* vbarK,
+                                 double* const* xbar0, double* const* vbar0, double* grad, void* stream) {
+  EnsArgs e;
+  FlowK f;
+  AdjWs w;
+  if (int r = adj_common(h, fl, K, ckpt_every, ws, ws_bytes, &e, &f, &w, "soax_step_adjoint")) return r;
+  if (!grad) return fail(SOAX_EINVAL, "soax_step_adjoint: grad is NULL");
+  cudaStream_t s = as_stream(stream);
+  if (h->n == 0) {
+    cudaError_t ce = cudaMemsetAsync(grad, 0, 4 * sizeof(double), s);
+    return ce == cudaSuccess ? SOAX_OK : cuda_fail(ce, "soax_step_adjoint: memset");
+  }
+  if (int r = check_ptrs3((const void* const*)xbarK, false, "xbarK")) return r;
+  if (int r = check_ptrs3((const void* const*)vbarK, true, "vbarK")) return r;
+  if (int r = check_ptrs3((const void* const*)xbar0, false, "xbar0")) return r;
+  if (int r = check_ptrs3((const void* const*)vbar0, false, "vbar0")) return r;
+  AdjIO io;
+  for (int c = 0; c < 3; ++c) {
+    io.xbK[c] = xbarK[c];
+    io.vbK[c] = vbarK ? vbarK[c] : nullptr;
+    io.xb0[c] = xbar0[c];
+    io.vb0[c] = vbar0[c];
+  }
+  char* base = static_cast<char*>(ws);
+  double* partials = reinterpret_cast<double*>(base + w.off_partials);
+  const int nb = grid_for(h->n, kAdjBlock);
+  k_adj_reverse<<<nb, kAdjBlock, 0, s>>>(e, f, K, ckpt_every, w.nck, base + w.off_ckpt, base + w.off_stack,
+                                        w.state_bytes, io, partials);
+  if (int r = check_launch("soax_step_adjoint")) return r;
+  k_reduce_partials<<<1, 256, 0, s>>>(partials, nb, 4, 1.0, grad);
+  return check_launch("soax_step_adjoint: reduce");
+}
+
+extern "C" int soax_minimage_loss(soax_t h, int32_t pos_field, const double* const* xtgt, double* loss,
+                                  double* const* xbar, void* ws, size_t ws_bytes, void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (int r = check_field(h, pos_field, SOAX_F64, 3, "soax_minimage_loss position")) return r;
+  if (!loss) return fail(SOAX_EINVAL, "soax_minimage_loss: loss is NULL");
+  if (h->n == 0) return fail(SOAX_EINVAL, "soax_minimage_loss: no particles");
+  if (int r = check_ptrs3((const void* const*)xtgt, false, "xtgt")) return r;
+  if (int r = check_ptrs3((const void* const*)xbar, true, "xbar")) return r;
+  const int nb = grid_for(h->n, kLossBlock);
+  if (!ws || ws_bytes < (size_t)nb * 8) return fail(SOAX_ENOMEM, "soax_minimage_loss: workspace too small");
+  if (!aligned16(ws)) return fail(SOAX_EALIGN, "soax_minimage_loss: workspace not 16-byte aligned");
+  LossIO io;
+  const int fp = h->fields[pos_field].first_plane;
+  for (int c = 0; c < 3; ++c) {
+    io.x[c] = (const double*)h->planes[h->current][fp + c];
+    if (!io.x[c]) return fail(SOAX_EUNBOUND, "soax_minimage_loss: position not bound");
+    io.xt[c] = xtgt[c];
+    io.xb[c] = xbar ? xbar[c] : nullptr;
+  }
+  double* partials = static_cast<double*>(ws);
+  cudaStream_t s = as_stream(stream);
+  k_minimage_loss<<<nb, kLossBlock, 0, s>>>(io, h->n, 2.0 / (double)h->n, partials);
+  if (int r = check_launch("soax_minimage_loss")) return r;
+  k_reduce_partials<<<1, 256, 0, s>>>(partials, nb, 1, 1.0 / (double)h->n, loss);
+  return check_launch("soax_minimage_loss: reduce");
+}

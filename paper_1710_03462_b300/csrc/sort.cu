@@ -1,0 +1,458 @@
+// Cell keys, stable LSD radix sort of (u32 key, u32 value) pairs, the permute-gather of
+// every plane, and soax_sort_by_cell which chains them.
+//
+// The sort keeps the particle arrays in spatial order so that the step's and the
+// gather's memory accesses stay local (Sec. 1 motivates SoA layouts by the spatial
+// locality of memory access; the sort extends that to the particles' order).
+//
+// Radix sort: reduce-then-scan, least significant digit first, digits of up to 9 bits.
+// Per pass: (1) every block histograms the digits of its 4096-key tile; (2) one block
+// per digit turns the per-block counts into global offsets (digit-major exclusive
+// scan); (3) every block ranks its tile stably (warp match + per-warp counters, in tile
+// order), stages the tile in shared memory in digit order and writes each digit's run
+// contiguously.  No block waits on another block, so nothing can hang.
+#include "soax_internal.h"
+
+namespace soax {
+
+constexpr int kSortBlock = 256;
+constexpr int kSortWarps = kSortBlock / 32;
+constexpr int kSortItems = 16;
+constexpr int kTile = kSortBlock * kSortItems;  // 4096 keys per block
+constexpr int kMaxDigitBits = 9;
+constexpr int kMaxRadix = 1 << kMaxDigitBits;
+constexpr int kScanThreads = 1024;
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct RadixPlan {
+  int passes = 0, width = 0;
+  int64_t nblocks = 0;
+  size_t off_counts = 0, off_totals = 0, off_ak[2] = {0, 0}, off_av[2] = {0, 0}, total = 0;
+};
+
+static RadixPlan radix_plan(int64_t n, int bits) {
+  RadixPlan p;
+  p.passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+  p.width = (bits + p.passes - 1) / p.passes;
+  p.nblocks = (n + kTile - 1) / kTile;
+  size_t off = 0;
+  p.off_counts = off;
+  off = align256(off + (size_t)kMaxRadix * p.nblocks * 4);
+  p.off_totals = off;
+  off = align256(off + (size_t)kMaxRadix * 4);
+  int nalt = p.passes <= 1 ? 0 : (p.passes == 2 ? 1 : 2);
+  for (int a = 0; a < nalt; ++a) {
+    p.off_ak[a] = off;
+    off = align256(off + (size_t)n * 4);
+    p.off_av[a] = off;
+    off = align256(off + (size_t)n * 4);
+  }
+  p.total = off;
+  return p;
+}
+
+// ------------------------------------------------------------------ block scans
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread over the block; returns this thread's prefix
+// and writes the block total to *total.  scratch: 33 words of shared memory.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratch, uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) scratch[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = lane < nw ? scratch[lane] : 0;
+    uint32_t si = warp_incl_scan(s);
+    if (lane < nw) scratch[lane] = si - s;
+    if (lane == nw - 1) scratch[32] = si;
+  }
+  __syncthreads();
+  uint32_t r = scratch[w] + inc - v;
+  uint32_t t = scratch[32];
+  __syncthreads();
+  *total = t;
+  return r;
+}
+
+// ------------------------------------------------------------------ cell keys
+__global__ void __launch_bounds__(256) k_cell_keys(const double* __restrict__ px, const double* __restrict__ py,
+                                                   const double* __restrict__ pz, int64_t n, double c, int G,
+                                                   uint32_t* __restrict__ keys) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int ix = min(__double2int_rz(__dmul_rn(px[i], c)), G - 1);
+  int iy = min(__double2int_rz(__dmul_rn(py[i], c)), G - 1);
+  int iz = min(__double2int_rz(__dmul_rn(pz[i], c)), G - 1);
+  keys[i] = (uint32_t)((iz * G + iy) * G + ix);
+}
+
+// ------------------------------------------------------------------ radix passes
+__global__ void __launch_bounds__(kSortBlock) k_radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                              uint32_t mask, int64_t nblocks,
+                                                              uint32_t* __restrict__ counts,
+                                                              uint32_t* __restrict__ totals) {
+  __shared__ uint32_t hist[kMaxRadix];
+  const int radix = (int)mask + 1, tid = threadIdx.x, lane = tid & 31;
+  for (int d = tid; d < radix; d += kSortBlock) hist[d] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  const uint32_t lt = (1u << lane) - 1;
+#pragma unroll 4
+  for (int j = 0; j < kSortItems; ++j) {
+    int64_t i = base + (int64_t)j * kSortBlock + tid;
+    bool valid = i < n;
+    uint32_t d = valid ? ((keys[i] >> shift) & mask) : 0xFFFFFFFFu;
+    // Warp-aggregated increment: sorted input puts many equal digits in one warp.
+    uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (valid && (peers & lt) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int d = tid; d < radix; d += kSortBlock) {
+    uint32_t c = hist[d];
+    counts[(int64_t)d * nblocks + blockIdx.x] = c;
+    if (c) atomicAdd(&totals[d], c);
+  }
+}
+
+// One block per digit d: counts[d][b] <- sum_{d' < d} totals[d'] + sum_{b' < b} counts[d][b'].
+__global__ void __launch_bounds__(kScanThreads) k_radix_scan_rows(uint32_t* __restrict__ counts,
+                                                                  const uint32_t* __restrict__ totals,
+                                                                  int64_t nblocks) {
+  __shared__ uint32_t scratch[33];
+  const int d = blockIdx.x, tid = threadIdx.x;
+  uint32_t part = 0;
+  for (int k = tid; k < d; k += kScanThreads) part += totals[k];
+  uint32_t base;
+  block_excl_scan(part, scratch, &base);
+  uint32_t* row = counts + (int64_t)d * nblocks;
+  const int64_t per = (nblocks + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = tid * per, hi = lo + per < nblocks ? lo + per : nblocks;
+  uint32_t s = 0;
+  for (int64_t k = lo; k < hi; ++k) s += row[k];
+  uint32_t tot;
+  uint32_t excl = block_excl_scan(s, scratch, &tot) + base;
+  for (int64_t k = lo; k < hi; ++k) {
+    uint32_t c = row[k];
+    row[k] = excl;
+    excl += c;
+  }
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_radix_downsweep(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, int64_t n, int shift, uint32_t mask, int64_t nblocks,
+    const uint32_t* __restrict__ counts) {
+  extern __shared__ uint32_t sm[];
+  const int radix = (int)mask + 1;
+  uint32_t* wc = sm;                         // [warps][radix]: per-warp digit counts, then prefixes
+  uint32_t* boff = wc + kSortWarps * radix;  // [radix]: block-local digit offsets
+  uint32_t* gbase = boff + radix;            // [radix]: global offset minus local offset
+  uint32_t* sk = gbase + radix;              // [tile] staged keys
+  uint32_t* sv = sk + kTile;                 // [tile] staged values
+  __shared__ uint32_t scratch[33];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int k = tid; k < kSortWarps * radix; k += kSortBlock) wc[k] = 0;
+  __syncthreads();
+  const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+  const int tcount = (int)(n - tile0 < kTile ? n - tile0 : kTile);
+  const uint32_t lt = (1u << lane) - 1;
+  uint32_t kr[kSortItems], vr[kSortItems], rk[kSortItems];
+  // Stable ranking: warp w owns tile elements [w*512, (w+1)*512) in rounds of 32.
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int li = w * (kTile / kSortWarps) + r * 32 + lane;
+    const bool valid = li < tcount;
+    const int64_t i = tile0 + li;
+    uint32_t key = valid ? keys_in[i] : 0u;
+    uint32_t val = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
+    uint32_t d = valid ? ((key >> shift) & mask) : 0xFFFFFFFFu;
+    uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t rank = 0;
+    if (valid) rank = wc[w * radix + d] + __popc(peers & lt);
+    __syncwarp();
+    if (valid && (peers & lt) == 0) wc[w * radix + d] += __popc(peers);
+    __syncwarp();
+    kr[r] = key;
+    vr[r] = val;
+    rk[r] = rank;
+  }
+  __syncthreads();
+  // Per digit: prefix over warps, block count.
+  for (int d = tid; d < radix; d += kSortBlock) {
+    uint32_t run = 0;
+    for (int ww = 0; ww < kSortWarps; ++ww) {
+      uint32_t c = wc[ww * radix + d];
+      wc[ww * radix + d] = run;
+      run += c;
+    }
+    boff[d] = run;
+  }
+  __syncthreads();
+  // Exclusive scan of the block's digit counts (radix <= 2 * kSortBlock).
+  {
+    const int d0 = 2 * tid, d1 = 2 * tid + 1;
+    uint32_t c0 = d0 < radix ? boff[d0] : 0, c1 = d1 < radix ? boff[d1] : 0, tot;
+    uint32_t ex = block_excl_scan(c0 + c1, scratch, &tot);
+    if (d0 < radix) boff[d0] = ex;
+    if (d1 < radix) boff[d1] = ex + c0;
+  }
+  __syncthreads();
+  for (int d = tid; d < radix; d += kSortBlock) gbase[d] = counts[(int64_t)d * nblocks + blockIdx.x] - boff[d];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int li = w * (kTile / kSortWarps) + r * 32 + lane;
+    if (li < tcount) {
+      uint32_t d = (kr[r] >> shift) & mask;
+      uint32_t lp = boff[d] + wc[w * radix + d] + rk[r];
+      sk[lp] = kr[r];
+      sv[lp] = vr[r];
+    }
+  }
+  __syncthreads();
+  for (int li = tid; li < tcount; li += kSortBlock) {
+    uint32_t key = sk[li];
+    uint32_t dest = gbase[(key >> shift) & mask] + (uint32_t)li;
+    if (keys_out) keys_out[dest] = key;
+    vals_out[dest] = sv[li];
+  }
+}
+
+static size_t downsweep_smem(int radix) { return (size_t)(kSortWarps * radix + 2 * radix + 2 * kTile) * 4; }
+
+// ------------------------------------------------------------------ permute
+struct PermArgs {
+  const void* in[kMaxPlanes];
+  void* out[kMaxPlanes];
+  int32_t es[kMaxPlanes];
+  int nplanes;
+  int64_t n;
+  const uint32_t* perm;
+};
+
+__global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArgs a) {
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i0 >= a.n) return;
+  if (i0 + 4 <= a.n) {
+    const uint4 p = *reinterpret_cast<const uint4*>(a.perm + i0);
+    for (int f = 0; f < a.nplanes; ++f) {
+      const int es = a.es[f];
+      if (es == 8) {
+        const unsigned long long* s = static_cast<const unsigned long long*>(a.in[f]);
+        unsigned long long* o = static_cast<unsigned long long*>(a.out[f]) + i0;
+        unsigned long long v0 = s[p.x], v1 = s[p.y], v2 = s[p.z], v3 = s[p.w];
+        reinterpret_cast<ulonglong2*>(o)[0] = make_ulonglong2(v0, v1);
+        reinterpret_cast<ulonglong2*>(o)[1] = make_ulonglong2(v2, v3);
+      } else if (es == 4) {
+        const uint32_t* s = static_cast<const uint32_t*>(a.in[f]);
+        *reinterpret_cast<uint4*>(static_cast<uint32_t*>(a.out[f]) + i0) = make_uint4(s[p.x], s[p.y], s[p.z], s[p.w]);
+      } else {
+        const uint8_t* s = static_cast<const uint8_t*>(a.in[f]);
+        uint32_t v = (uint32_t)s[p.x] | ((uint32_t)s[p.y] << 8) | ((uint32_t)s[p.z] << 16) | ((uint32_t)s[p.w] << 24);
+        *reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(a.out[f]) + i0) = v;
+      }
+    }
+  } else {
+    for (int64_t i = i0; i < a.n; ++i) {
+      const uint32_t p = a.perm[i];
+      for (int f = 0; f < a.nplanes; ++f) {
+        const int es = a.es[f];
+        if (es == 8)
+          static_cast<unsigned long long*>(a.out[f])[i] = static_cast<const unsigned long long*>(a.in[f])[p];
+        else if (es == 4)
+          static_cast<uint32_t*>(a.out[f])[i] = static_cast<const uint32_t*>(a.in[f])[p];
+        else
+          static_cast<uint8_t*>(a.out[f])[i] = static_cast<const uint8_t*>(a.in[f])[p];
+      }
+    }
+  }
+}
+
+static int key_bits_for_grid(int G) {
+  uint32_t maxkey = (uint32_t)G * G * G - 1;
+  int b = 0;
+  while (b < 32 && (maxkey >> b)) ++b;
+  return b < 1 ? 1 : b;
+}
+
+struct SortWs {
+  size_t off_keys, off_skeys, off_perm, off_radix, total;
+  RadixPlan rp;
+};
+
+static SortWs sort_ws_plan(int64_t n, int G) {
+  SortWs w;
+  size_t off = 0;
+  w.off_keys = off;
+  off = align256(off + (size_t)n * 4);
+  w.off_skeys = off;
+  off = align256(off + (size_t)n * 4);
+  w.off_perm = off;
+  off = align256(off + (size_t)n * 4);
+  w.off_radix = off;
+  w.rp = radix_plan(n, key_bits_for_grid(G));
+  w.total = off + w.rp.total;
+  return w;
+}
+
+static int find_position_field(soax_t h) {
+  for (size_t f = 0; f < h->fields.size(); ++f)
+    if (h->fields[f].tag == 'P' && h->fields[f].dtype == SOAX_F64 && h->fields[f].ncomp == 3) return (int)f;
+  return -1;
+}
+
+}  // namespace soax
+
+using namespace soax;
+
+extern "C" int soax_cell_keys(soax_t h, int32_t pos_field, int32_t grid, uint32_t* keys, void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (int r = check_field(h, pos_field, SOAX_F64, 3, "soax_cell_keys position")) return r;
+  if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, "soax_cell_keys: grid must be in 1..1024");
+  if (h->n == 0) return SOAX_OK;
+  if (!keys) return fail(SOAX_EINVAL, "soax_cell_keys: keys is NULL");
+  if (!aligned16(keys)) return fail(SOAX_EALIGN, "soax_cell_keys: keys not 16-byte aligned");
+  const int fp = h->fields[pos_field].first_plane;
+  const double* px = (const double*)h->planes[h->current][fp];
+  const double* py = (const double*)h->planes[h->current][fp + 1];
+  const double* pz = (const double*)h->planes[h->current][fp + 2];
+  if (!px || !py || !pz) return fail(SOAX_EUNBOUND, "soax_cell_keys: position planes not bound");
+  const double c = (double)grid / SOAX_TWO_PI_HOST;
+  k_cell_keys<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n, c, grid, keys);
+  return check_launch("soax_cell_keys");
+}
+
+extern "C" int soax_radix_workspace_bytes(int64_t n, int32_t key_bits, size_t* bytes) {
+  if (!bytes) return fail(SOAX_EINVAL, "soax_radix_workspace_bytes: NULL");
+  if (n < 0 || n >= (int64_t(1) << 31)) return fail(SOAX_EINVAL, "soax_radix_workspace_bytes: n out of range");
+  if (key_bits < 1 || key_bits > 32) return fail(SOAX_EINVAL, "soax_radix_workspace_bytes: key_bits in 1..32");
+  *bytes = radix_plan(n, key_bits).total;
+  return SOAX_OK;
+}
+
+extern "C" int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                     uint32_t* vals_out, int64_t n, int32_t key_bits, void* ws, size_t ws_bytes,
+                                     void* stream) {
+  if (n < 0 || n >= (int64_t(1) << 31)) return fail(SOAX_EINVAL, "soax_radix_sort_pairs: n out of range");
+  if (key_bits < 1 || key_bits > 32) return fail(SOAX_EINVAL, "soax_radix_sort_pairs: key_bits in 1..32");
+  if (n == 0) return SOAX_OK;
+  if (!keys_in || !vals_out || !ws) return fail(SOAX_EINVAL, "soax_radix_sort_pairs: NULL pointer");
+  if (!aligned16(keys_in) || !aligned16(vals_in) || !aligned16(keys_out) || !aligned16(vals_out) || !aligned16(ws))
+    return fail(SOAX_EALIGN, "soax_radix_sort_pairs: pointers must be 16-byte aligned");
+  if (keys_out == keys_in || (vals_in && vals_out == vals_in) || (const uint32_t*)vals_out == keys_in)
+    return fail(SOAX_EINVAL, "soax_radix_sort_pairs: outputs must not alias inputs");
+  RadixPlan p = radix_plan(n, key_bits);
+  if (ws_bytes < p.total) return fail(SOAX_ENOMEM, "soax_radix_sort_pairs: workspace too small");
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)downsweep_smem(kMaxRadix));
+    if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: smem attribute");
+    attr_set[dev] = true;
+  }
+  char* w = static_cast<char*>(ws);
+  uint32_t* counts = reinterpret_cast<uint32_t*>(w + p.off_counts);
+  uint32_t* totals = reinterpret_cast<uint32_t*>(w + p.off_totals);
+  uint32_t* ak[2] = {reinterpret_cast<uint32_t*>(w + p.off_ak[0]), reinterpret_cast<uint32_t*>(w + p.off_ak[1])};
+  uint32_t* av[2] = {reinterpret_cast<uint32_t*>(w + p.off_av[0]), reinterpret_cast<uint32_t*>(w + p.off_av[1])};
+  cudaStream_t s = as_stream(stream);
+  for (int pass = 0; pass < p.passes; ++pass) {
+    const int shift = pass * p.width;
+    const int width = key_bits - shift < p.width ? key_bits - shift : p.width;
+    const uint32_t mask = (uint32_t)((1u << width) - 1);
+    const int radix = (int)mask + 1;
+    const bool last = pass == p.passes - 1;
+    const uint32_t* kin = pass == 0 ? keys_in : ak[(pass - 1) & 1];
+    const uint32_t* vin = pass == 0 ? vals_in : av[(pass - 1) & 1];
+    uint32_t* kout = last ? keys_out : ak[pass & 1];
+    uint32_t* vout = last ? vals_out : av[pass & 1];
+    cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)radix * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: memset");
+    k_radix_upsweep<<<(unsigned)p.nblocks, kSortBlock, 0, s>>>(kin, n, shift, mask, p.nblocks, counts, totals);
+    if (int r = check_launch("radix upsweep")) return r;
+    k_radix_scan_rows<<<radix, kScanThreads, 0, s>>>(counts, totals, p.nblocks);
+    if (int r = check_launch("radix scan")) return r;
+    k_radix_downsweep<<<(unsigned)p.nblocks, kSortBlock, downsweep_smem(radix), s>>>(kin, vin, kout, vout, n, shift,
+                                                                                    mask, p.nblocks, counts);
+    if (int r = check_launch("radix downsweep")) return r;
+  }
+  return SOAX_OK;
+}
+
+extern "C" int soax_permute(soax_t h, const uint32_t* perm, void* stream) {
+  if (int r = check_handle(h)) return r;
+  const int src = h->current, dst = src ^ 1;
+  if (h->n == 0) {
+    h->current = dst;
+    return SOAX_OK;
+  }
+  if (!perm) return fail(SOAX_EINVAL, "soax_permute: perm is NULL");
+  if (!aligned16(perm)) return fail(SOAX_EALIGN, "soax_permute: perm not 16-byte aligned");
+  if (int r = live_planes_bound(h, src)) return r;
+  if (int r = live_planes_bound(h, dst)) return r;
+  PermArgs a;
+  for (int p = 0; p < h->nplanes; ++p) {
+    a.in[p] = h->planes[src][p];
+    a.out[p] = h->planes[dst][p];
+    a.es[p] = h->plane_esize[p];
+  }
+  a.nplanes = h->nplanes;
+  a.n = h->n;
+  a.perm = perm;
+  k_permute<<<grid_for((h->n + 3) / 4, 256), 256, 0, as_stream(stream)>>>(a);
+  if (int r = check_launch("soax_permute")) return r;
+  h->current = dst;
+  return SOAX_OK;
+}
+
+extern "C" int soax_sort_workspace_bytes(soax_t h, int32_t grid, size_t* bytes) {
+  if (int r = check_handle(h)) return r;
+  if (!bytes) return fail(SOAX_EINVAL, "soax_sort_workspace_bytes: NULL");
+  if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, "soax_sort_workspace_bytes: grid must be in 1..1024");
+  *bytes = sort_ws_plan(h->n, grid).total;
+  return SOAX_OK;
+}
+
+extern "C" int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
+                                 uint32_t** perm) {
+  if (int r = check_handle(h)) return r;
+  if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, "soax_sort_results: grid must be in 1..1024");
+  SortWs w = sort_ws_plan(h->n, grid);
+  if (!ws || ws_bytes < w.total) return fail(SOAX_ENOMEM, "soax_sort_results: workspace too small");
+  if (sorted_keys) *sorted_keys = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + w.off_skeys);
+  if (perm) *perm = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + w.off_perm);
+  return SOAX_OK;
+}
+
+extern "C" int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_bytes, void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, "soax_sort_by_cell: grid must be in 1..1024");
+  const int pf = find_position_field(h);
+  if (pf < 0) return fail(SOAX_ESCHEMA, "soax_sort_by_cell: no f64 x 3 field tagged 'P'");
+  SortWs w = sort_ws_plan(h->n, grid);
+  if (h->n == 0) return SOAX_OK;
+  if (!ws || ws_bytes < w.total) return fail(SOAX_ENOMEM, "soax_sort_by_cell: workspace too small");
+  if (!aligned16(ws)) return fail(SOAX_EALIGN, "soax_sort_by_cell: workspace not 16-byte aligned");
+  if (int r = live_planes_bound(h, h->current)) return r;
+  if (int r = live_planes_bound(h, h->current ^ 1)) return r;
+  char* base = static_cast<char*>(ws);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(base + w.off_keys);
+  uint32_t* skeys = reinterpret_cast<uint32_t*>(base + w.off_skeys);
+  uint32_t* perm = reinterpret_cast<uint32_t*>(base + w.off_perm);
+  if (int r = soax_cell_keys(h, pf, grid, keys, stream)) return r;
+  if (int r = soax_radix_sort_pairs(keys, nullptr, skeys, perm, h->n, key_bits_for_grid(grid), base + w.off_radix,
+                                    w.rp.total, stream))
+    return r;
+  return soax_permute(h, perm, stream);
+}

@@ -1,0 +1,156 @@
+// soax_step (SoA) and soax_step_aos: one pass over memory per midpoint-RK2 step.
+#include <cmath>
+
+#include "soax_internal.h"
+#include "step_core.cuh"
+
+namespace soax {
+
+int make_ens_args(soax_t h, const soax_flow* fl, int buf, EnsArgs* e, FlowK* f, const char* who) {
+  std::string w(who);
+  if (!fl) return fail(SOAX_EINVAL, w + ": flow is NULL");
+  if (!(fl->dt > 0.0) || !std::isfinite(fl->dt)) return fail(SOAX_EINVAL, w + ": dt must be finite and > 0");
+  if (!std::isfinite(fl->A) || !std::isfinite(fl->B) || !std::isfinite(fl->C))
+    return fail(SOAX_EINVAL, w + ": flow amplitudes must be finite");
+  if (int r = check_field(h, fl->pos_field, SOAX_F64, 3, "position")) return r;
+  if (int r = check_field(h, fl->vel_field, SOAX_F32, 3, "velocity")) return r;
+  if (fl->acc_field >= 0) {
+    if (int r = check_field(h, fl->acc_field, SOAX_F32, 3, "acceleration")) return r;
+  } else if (fl->acc_field != -1) {
+    return fail(SOAX_ESCHEMA, w + ": acc_field must be -1 or a field index");
+  }
+  if (fl->tau_field >= 0) {
+    if (int r = check_field(h, fl->tau_field, SOAX_F32, 1, "tau source")) return r;
+    if (!(fl->tau_scale > 0.0) || !std::isfinite(fl->tau_scale))
+      return fail(SOAX_EINVAL, w + ": tau_scale must be finite and > 0");
+  } else {
+    if (fl->tau_field != -1) return fail(SOAX_ESCHEMA, w + ": tau_field must be -1 or a field index");
+    if (!(fl->tau > 0.0) || !std::isfinite(fl->tau)) return fail(SOAX_EINVAL, w + ": tau must be finite and > 0");
+  }
+  auto plane = [&](int field, int comp) -> void* { return h->planes[buf][h->fields[field].first_plane + comp]; };
+  e->px = (double*)plane(fl->pos_field, 0);
+  e->py = (double*)plane(fl->pos_field, 1);
+  e->pz = (double*)plane(fl->pos_field, 2);
+  e->vx = (float*)plane(fl->vel_field, 0);
+  e->vy = (float*)plane(fl->vel_field, 1);
+  e->vz = (float*)plane(fl->vel_field, 2);
+  e->ax = e->ay = e->az = nullptr;
+  if (fl->acc_field >= 0) {
+    e->ax = (float*)plane(fl->acc_field, 0);
+    e->ay = (float*)plane(fl->acc_field, 1);
+    e->az = (float*)plane(fl->acc_field, 2);
+  }
+  e->tau_src = fl->tau_field >= 0 ? (const float*)plane(fl->tau_field, 0) : nullptr;
+  e->n = h->n;
+  e->A = fl->A;
+  e->B = fl->B;
+  e->C = fl->C;
+  e->inv_tau = fl->tau_field >= 0 ? 0.0 : 1.0 / fl->tau;
+  e->tau_scale = fl->tau_scale;
+  if (h->n > 0) {
+    if (!e->px || !e->py || !e->pz || !e->vx || !e->vy || !e->vz ||
+        (fl->acc_field >= 0 && (!e->ax || !e->ay || !e->az)) || (fl->tau_field >= 0 && !e->tau_src))
+      return fail(SOAX_EUNBOUND, w + ": a plane the step needs is not bound");
+  }
+  f->A = fl->A;
+  f->B = fl->B;
+  f->C = fl->C;
+  f->dt = fl->dt;
+  f->hdt = 0.5 * fl->dt;
+  return SOAX_OK;
+}
+
+constexpr int kStepPPT = 4;
+constexpr int kStepBlock = 256;
+
+template <int PPT, int VB>
+__global__ void __launch_bounds__(kStepBlock) k_step_soa(EnsArgs e, FlowK f) {
+  int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * PPT;
+  if (i0 >= e.n) return;
+  if (i0 + PPT <= e.n)
+    step_group<PPT, VB>(e, f, i0, 1);
+  else
+    step_tail(e, f, i0, (int)(e.n - i0), 1);
+}
+
+struct AosArgs {
+  char* rec;
+  int64_t R, pos_off, vel_off, acc_off, tau_off;  // offsets in bytes; -1 = absent
+  int64_t n;
+  double A, B, C, inv_tau, tau_scale;
+};
+
+__global__ void __launch_bounds__(256) k_step_aos(AosArgs a, FlowK fdt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const FlowK f{a.A, a.B, a.C, fdt.dt, fdt.hdt};
+  char* r = a.rec + i * a.R;
+  const double* pp = reinterpret_cast<const double*>(r + a.pos_off);
+  const float* vp = reinterpret_cast<const float*>(r + a.vel_off);
+  double p[3] = {pp[0], pp[1], pp[2]};
+  float v[3] = {vp[0], vp[1], vp[2]}, acc[3];
+  double it = a.inv_tau;
+  if (a.tau_off >= 0) it = 1.0 / __dmul_rn(a.tau_scale, (double)*reinterpret_cast<const float*>(r + a.tau_off));
+  rk2_step(f, it, p, v, acc);
+  double* pw = reinterpret_cast<double*>(r + a.pos_off);
+  float* vw = reinterpret_cast<float*>(r + a.vel_off);
+  pw[0] = p[0]; pw[1] = p[1]; pw[2] = p[2];
+  vw[0] = v[0]; vw[1] = v[1]; vw[2] = v[2];
+  if (a.acc_off >= 0) {
+    float* aw = reinterpret_cast<float*>(r + a.acc_off);
+    aw[0] = acc[0]; aw[1] = acc[1]; aw[2] = acc[2];
+  }
+}
+
+}  // namespace soax
+
+using namespace soax;
+
+extern "C" int soax_step(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (nsteps < 0) return fail(SOAX_EINVAL, "soax_step: nsteps < 0");
+  EnsArgs e;
+  FlowK f;
+  if (int r = make_ens_args(h, fl, h->current, &e, &f, "soax_step")) return r;
+  if (h->n == 0 || nsteps == 0) return SOAX_OK;
+  int grid = grid_for((h->n + kStepPPT - 1) / kStepPPT, kStepBlock);
+  cudaStream_t s = as_stream(stream);
+  for (int k = 0; k < nsteps; ++k) {
+    k_step_soa<kStepPPT, 128><<<grid, kStepBlock, 0, s>>>(e, f);
+    if (int r = check_launch("soax_step")) return r;
+  }
+  return SOAX_OK;
+}
+
+extern "C" int soax_step_aos(soax_t h, void* aos_dev, const soax_flow* fl, int32_t nsteps, void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (nsteps < 0) return fail(SOAX_EINVAL, "soax_step_aos: nsteps < 0");
+  if (!aos_dev && h->n > 0) return fail(SOAX_EINVAL, "soax_step_aos: NULL records");
+  if (!aligned16(aos_dev)) return fail(SOAX_EALIGN, "soax_step_aos: records not 16-byte aligned");
+  // Validate the flow against the schema; the planes are not used, so pretend they are bound.
+  EnsArgs e;
+  FlowK f;
+  soax_s probe = *h;
+  for (int p = 0; p < probe.nplanes; ++p) probe.planes[0][p] = (void*)16;
+  if (int r = make_ens_args(&probe, fl, 0, &e, &f, "soax_step_aos")) return r;
+  if (h->n == 0 || nsteps == 0) return SOAX_OK;
+  AosArgs a;
+  a.rec = (char*)aos_dev;
+  a.R = h->record_bytes;
+  a.pos_off = h->offsets[fl->pos_field];
+  a.vel_off = h->offsets[fl->vel_field];
+  a.acc_off = fl->acc_field >= 0 ? h->offsets[fl->acc_field] : -1;
+  a.tau_off = fl->tau_field >= 0 ? h->offsets[fl->tau_field] : -1;
+  a.n = h->n;
+  a.A = e.A;
+  a.B = e.B;
+  a.C = e.C;
+  a.inv_tau = e.inv_tau;
+  a.tau_scale = e.tau_scale;
+  // One pass over the records per step, like soax_step.
+  for (int k = 0; k < nsteps; ++k) {
+    k_step_aos<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(a, f);
+    if (int r = check_launch("soax_step_aos")) return r;
+  }
+  return SOAX_OK;
+}

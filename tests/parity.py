@@ -1,0 +1,73 @@
+"""Shared helpers of the GPU parity tests: compare a GPU state with the oracle's and
+audit every particle outside the tolerance.
+
+Tolerances (100-step state): positions max |dx| <= 1e-11; velocities
+|dv| <= 1e-5 |v_ref| with a floor of 1e-9 absolute (v0 ~ N(0, 0.1^2) can be near 0).
+
+Audit: the f32 storage of v makes the path sensitive to f64 differences of a few ulp
+that move v + dt a2 across an f32 rounding midpoint; one such flip changes v by one
+f32 ulp and the position by ~tau * ulp.  A particle out of tolerance is replayed one
+step at a time on the GPU and in the oracle from the same state; every step must give
+positions within 1e-13, and velocities must be equal or one f32 ulp apart with the
+oracle's f64 value within 1e-14 (relative) of the f32 midpoint between them.
+"""
+import numpy as np
+import torch
+
+import oracle
+import paper_1710_03462_b300 as sx
+
+POS_TOL = 1e-11
+VEL_RTOL = 1e-5
+VEL_ATOL = 1e-9
+
+
+def out_of_tolerance(gpos, gvel, opos, ovel):
+    """Boolean mask of particles whose GPU state misses the tolerance."""
+    bad = np.zeros(gpos[0].size, bool)
+    for c in range(3):
+        d = np.abs(gpos[c] - opos[c])
+        d = np.minimum(d, sx.TWO_PI - d)  # the same point seen across the periodic wrap
+        bad |= d > POS_TOL
+        bad |= np.abs(gvel[c].astype(np.float64) - ovel[c]) > np.maximum(VEL_RTOL * np.abs(ovel[c]), VEL_ATOL)
+    return bad
+
+
+def gpu_one_step(x3, v3, A, B, C, tau, dt):
+    p = sx.Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], 1, shadow=False)
+    p.load({"pos": [np.array([x]) for x in x3], "vel": [np.array([v], np.float32) for v in v3]})
+    p.step(sx.Flow(A=A, B=B, C=C, tau=tau, dt=dt), 1)
+    d = p.numpy()
+    return np.array([a[0] for a in d["pos"]]), np.array([a[0] for a in d["vel"]], np.float32)
+
+
+def audit_particle(x0, v0, A, B, C, tau, dt, steps):
+    """Replay one particle; returns the number of accepted midpoint flips or raises."""
+    x = np.array(x0, np.float64)
+    v = np.array(v0, np.float32)
+    flips = 0
+    for s in range(steps):
+        gx, gv = gpu_one_step(x, v, A, B, C, tau, dt)
+        ox, ovn, _ = oracle.step_one_detail(A, B, C, tau, dt, x, v)
+        ov = ovn.astype(np.float32)
+        dx = np.abs(gx - ox)
+        dx = np.minimum(dx, sx.TWO_PI - dx)
+        assert np.all(dx <= 1e-13), f"step {s}: position differs by {dx.max()}"
+        for c in range(3):
+            if gv[c] != ov[c]:
+                gap = abs(np.nextafter(ov[c], gv[c], dtype=np.float32) - gv[c])
+                assert gap == 0, f"step {s}: velocity differs by more than one f32 ulp"
+                mid = (np.float64(gv[c]) + np.float64(ov[c])) / 2
+                assert abs(ovn[c] - mid) <= 1e-14 * abs(ovn[c]), f"step {s}: flip away from an f32 midpoint"
+                flips += 1
+        x, v = ox, ov
+    return flips
+
+
+def assert_parity(gpos, gvel, opos, ovel, x0, v0, taus, A, B, C, dt, steps, max_audit=20):
+    """Tolerance check, with an audit of each particle out of tolerance."""
+    bad = np.flatnonzero(out_of_tolerance(gpos, gvel, opos, ovel))
+    assert bad.size <= max_audit, f"{bad.size} particles out of tolerance"
+    for i in bad:
+        audit_particle([x0[c][i] for c in range(3)], [v0[c][i] for c in range(3)], A, B, C, float(taus[i]), dt, steps)
+    return bad.size

@@ -1,0 +1,115 @@
+"""The C ABI without a GPU: the library builds and loads, exports every symbol that
+include/soax.h declares, and validates arguments on the host (no device work)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1710_03462_b300 as sx
+from paper_1710_03462_b300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "soax.h")).read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(soax_\w+)\s*\(", src, re.M)))
+
+
+def test_exports_every_declared_symbol():
+    L = sx.lib()
+    names = _declared()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(_abi.EXPORTS) == names
+
+
+def _create(schema, n):
+    descs = (_abi.soax_field_desc * len(schema))()
+    keep = []
+    for k, (name, dt, nc, tag) in enumerate(schema):
+        b = name.encode()
+        keep.append(b)
+        descs[k] = _abi.soax_field_desc(b, _abi.DTYPES.get(dt, 99), nc, tag.encode())
+    h = C.c_void_p()
+    rc = sx.lib().soax_create(descs, len(schema), n, C.byref(h))
+    return rc, h
+
+
+def test_version_and_layout():
+    L = sx.lib()
+    assert L.soax_version() == 1
+    rc, h = _create(sx.WIDE_SCHEMA, 10)
+    assert rc == 0
+    rb = C.c_int64()
+    offs = (C.c_int64 * 6)()
+    assert L.soax_aos_layout(h, C.byref(rb), offs) == 0
+    assert (rb.value, list(offs)) == (64, [0, 8, 32, 44, 56, 60])
+    n, nf, npl = C.c_int64(), C.c_int32(), C.c_int32()
+    assert L.soax_size(h, C.byref(n), C.byref(nf), C.byref(npl)) == 0
+    assert (n.value, nf.value, npl.value) == (10, 6, 12)
+    assert L.soax_destroy(h) == 0
+
+
+@pytest.mark.parametrize("schema,n", [
+    ([("a", "f99", 1, "x")], 4),
+    ([("a", "f32", 0, "x")], 4),
+    ([("a", "f32", 17, "x")], 4),
+    ([("a", "f32", 1, "x"), ("a", "f64", 1, "y")], 4),
+    ([("", "f32", 1, "x")], 4),
+    ([(f"f{k}", "f32", 16, "x") for k in range(5)], 4),
+])
+def test_bad_schemas(schema, n):
+    rc, h = _create(schema, n)
+    assert rc == -2 and not h.value
+
+
+def test_bad_sizes():
+    assert _create(sx.BASIC_SCHEMA, -1)[0] == -1
+    assert _create(sx.BASIC_SCHEMA, 2 ** 31)[0] == -1
+
+
+def test_bind_validation_and_step_validation_without_gpu():
+    L = sx.lib()
+    rc, h = _create(sx.BASIC_SCHEMA, 100)
+    assert L.soax_bind(h, 1, 0, 0, C.c_void_p(0x1008)) == -3   # misaligned
+    assert L.soax_bind(h, 1, 3, 0, C.c_void_p(0x1000)) == -1   # bad component
+    assert L.soax_bind(h, 5, 0, 0, C.c_void_p(0x1000)) == -1   # bad field
+    assert L.soax_bind(h, 1, 0, 2, C.c_void_p(0x1000)) == -1   # bad buffer
+    assert L.soax_bind(h, 1, 0, 0, None) == -1
+    fl = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 1, 2, -1)
+    assert L.soax_step(h, C.byref(fl), 1, None) == -8           # planes not bound
+    bad = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 2, 1, -1)  # pos/vel swapped
+    assert L.soax_step(h, C.byref(bad), 1, None) == -2
+    neg = _abi.soax_flow(1, 1, 1, -0.1, 1e-3, 0.0, -1, 1, 2, -1)
+    assert L.soax_step(h, C.byref(neg), 1, None) == -1
+    assert L.soax_step(h, C.byref(fl), -1, None) == -1
+    assert b"nsteps" in L.soax_last_error()
+    assert L.soax_step(None, C.byref(fl), 1, None) == -1
+    L.soax_destroy(h)
+
+
+def test_empty_handle_is_a_no_op():
+    L = sx.lib()
+    rc, h = _create(sx.BASIC_SCHEMA, 0)
+    fl = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 1, 2, -1)
+    assert L.soax_step(h, C.byref(fl), 3, None) == 0
+    assert L.soax_soa_to_aos(h, None, None) == 0
+    L.soax_destroy(h)
+
+
+def test_workspace_sizes():
+    L = sx.lib()
+    b = C.c_size_t()
+    assert L.soax_radix_workspace_bytes(1 << 24, 15, C.byref(b)) == 0
+    # 2 passes: counts (512 x 4096 x 4) + totals + one ping-pong pair of n u32.
+    assert b.value >= 2 * 4 * (1 << 24)
+    assert L.soax_radix_workspace_bytes(10, 0, C.byref(b)) == -1
+    rc, h = _create(sx.BASIC_SCHEMA, 1000)
+    assert L.soax_sort_workspace_bytes(h, 32, C.byref(b)) == 0 and b.value > 3 * 4000
+    assert L.soax_adjoint_workspace_bytes(h, 1000, 32, C.byref(b)) == 0
+    assert b.value >= (32 + 32) * 36 * 1000
+    L.soax_destroy(h)

@@ -1,0 +1,141 @@
+"""GPU checkpointed forward and adjoint against the oracle's adjoint (f32-stored forward,
+same arithmetic) and against central finite differences; the autograd Function."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1710_03462_b300 as sx
+import soax_inputs
+
+pytestmark = pytest.mark.gpu
+
+SCHEMA = [("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")]
+
+
+def _target(d, K, A=1.1, tau=0.1, dt=1e-3):
+    xt = [a.copy() for a in d["pos"]]
+    vt = [a.copy() for a in d["vel"]]
+    oracle.step_soa(xt, vt, A, 1.0, 1.0, tau, dt, K)
+    return xt
+
+
+def _gpu_adjoint(d, xt, K, C, th, dt=1e-3):
+    n = d["pos"][0].size
+    p = sx.Particles(SCHEMA, n, shadow=False)
+    p.load({"pos": d["pos"], "vel": d["vel"]})
+    f = sx.Flow(A=th[0], B=th[1], C=th[2], tau=th[3], dt=dt)
+    ws = p.adjoint_workspace(K, C)
+    p.step_checkpointed(f, K, C, ws)
+    xtg = [torch.from_numpy(a).cuda() for a in xt]
+    loss, xbK = p.minimage_loss(xtg, ws)
+    xb0, vb0, g = p.step_adjoint(f, K, C, ws, xbK)
+    return (p, float(loss.item()), [t.cpu().numpy() for t in xb0], [t.cpu().numpy() for t in vb0],
+            g.cpu().numpy())
+
+
+@pytest.mark.parametrize("n,K,C", [(1, 5, 32), (1000, 70, 32), (4099, 100, 32), (513, 64, 8)])
+def test_adjoint_vs_oracle(n, K, C):
+    d = soax_inputs.basic_set(n, n)
+    xt = _target(d, K)
+    th = [1.0, 0.95, 1.05, 0.12]
+    p, loss, xb, vb, g = _gpu_adjoint(d, xt, K, C, th)
+    ol, oxb, ovb, og = oracle.adjoint(d["pos"], d["vel"], xt, *th, 1e-3, K, f32v=True)
+    assert abs(loss - ol) <= 1e-9 * abs(ol)
+    assert np.allclose(g, og, rtol=1e-9, atol=0)
+    for c in range(3):
+        scale = max(np.abs(oxb[c]).max(), 1e-300)
+        assert np.max(np.abs(xb[c] - oxb[c])) <= 1e-9 * scale
+        scale = max(np.abs(ovb[c]).max(), 1e-300)
+        assert np.max(np.abs(vb[c] - ovb[c])) <= 1e-9 * scale
+
+
+def test_checkpointed_forward_equals_plain_step():
+    n, K = 20000, 77
+    d = soax_inputs.basic_set(n, 3)
+    a = sx.Particles(SCHEMA, n, shadow=False)
+    a.load({"pos": d["pos"], "vel": d["vel"]})
+    b = sx.Particles(SCHEMA, n, shadow=False)
+    b.load({"pos": d["pos"], "vel": d["vel"]})
+    f = sx.Flow()
+    a.step(f, K)
+    ws = b.adjoint_workspace(K, 32)
+    b.step_checkpointed(f, K, 32, ws)
+    x, y = a.numpy(), b.numpy()
+    for k in x:
+        for u, v in zip(x[k], y[k]):
+            assert u.tobytes() == v.tobytes()
+
+
+def test_zero_gradient_at_target():
+    n, K = 2000, 64
+    d = soax_inputs.basic_set(n, 4)
+    xt = [a.copy() for a in d["pos"]]
+    vt = [a.copy() for a in d["vel"]]
+    oracle.step_soa(xt, vt, 1.1, 1.0, 1.0, 0.1, 1e-3, K)
+    p, loss, xb, vb, g = _gpu_adjoint(d, xt, K, 32, [1.1, 1.0, 1.0, 0.1])
+    assert loss == 0.0 and np.all(g == 0.0)
+    assert all(np.all(a == 0) for a in xb + vb)
+
+
+def test_gradients_vs_central_fd_of_fp64_forward():
+    """The GPU adjoint (f32-stored v) against finite differences of the oracle's FP64-state
+    forward; the gap is set by the f32 storage, hence the 1e-4 tolerance."""
+    n, K, eps = 256, 200, 1e-6
+    d = soax_inputs.basic_set(n, 6)
+    xt = _target(d, K)
+    th = [1.0, 1.0, 1.0, 0.1]
+    _, loss, xb, vb, g = _gpu_adjoint(d, xt, K, 32, th)
+
+    def L(t, vel=None):
+        p = [a.copy() for a in d["pos"]]
+        v = [a.astype(np.float64) for a in (vel or d["vel"])]
+        oracle.step_f64state(p, v, *t, 1e-3, K)
+        return sum(float(np.sum(((p[c] - xt[c] + np.pi) % (2 * np.pi) - np.pi) ** 2)) for c in range(3)) / n
+    for k in range(4):
+        tp, tm = list(th), list(th)
+        tp[k] += eps
+        tm[k] -= eps
+        fd = (L(tp) - L(tm)) / (2 * eps)
+        assert abs(g[k] - fd) <= 1e-4 * abs(fd) + 1e-10, (k, g[k], fd)
+
+
+def test_autograd_function():
+    n, K = 3000, 50
+    d = soax_inputs.basic_set(n, 7)
+    xt = _target(d, K)
+    x0 = torch.from_numpy(np.stack(d["pos"])).cuda().requires_grad_()
+    v0 = torch.from_numpy(np.stack(d["vel"]).astype(np.float64)).cuda().requires_grad_()
+    theta = torch.tensor([1.0, 0.9, 1.1, 0.1], dtype=torch.float64, device="cuda", requires_grad=True)
+    xk = sx.SoaxRK2.apply(x0, v0, theta, 1e-3, K, 32)
+    dd = xk - torch.from_numpy(np.stack(xt)).cuda()
+    dd = torch.remainder(dd + np.pi, 2 * np.pi) - np.pi
+    loss = (dd * dd).sum() / n
+    loss.backward()
+    ol, oxb, ovb, og = oracle.adjoint(d["pos"], d["vel"], xt, 1.0, 0.9, 1.1, 0.1, 1e-3, K, f32v=True)
+    assert np.allclose(theta.grad.cpu().numpy(), og, rtol=1e-8)
+    assert np.allclose(v0.grad.cpu().numpy(), np.stack(ovb), rtol=1e-8, atol=1e-14)
+    assert np.allclose(x0.grad.cpu().numpy(), np.stack(oxb), rtol=1e-8, atol=1e-14)
+
+
+def test_full_size_adjoint_n1M_sampled():
+    """The 1M-particle, K=1000 workload: per-particle gradients on every 1024th particle
+    against the oracle (each particle's adjoint depends only on itself and 1/n)."""
+    w = soax_inputs.WORKLOADS["adjoint_n1M"]
+    n, K, C = w["n"], w["K"], w["ckpt_every"]
+    d = soax_inputs.basic_set(n, w["seed"])
+    idx = np.arange(0, n, 1024)
+    sub = {k: [np.ascontiguousarray(a[idx]) for a in d[k]] for k in ("pos", "vel")}
+    xt_sub = _target(sub, K, A=w["A_target"], tau=w["tau"], dt=w["dt"])
+    xt = [a.copy() for a in d["pos"]]
+    for c in range(3):
+        xt[c][idx] = xt_sub[c]
+    th = [w["A"], w["B"], w["C"], w["tau"]]
+    _, loss, xb, vb, g = _gpu_adjoint(d, xt, K, C, th, dt=w["dt"])
+    ol, oxb, ovb, og = oracle.adjoint(sub["pos"], sub["vel"], xt_sub, *th, w["dt"], K, f32v=True)
+    scale = idx.size / n
+    for c in range(3):
+        assert np.allclose(xb[c][idx], oxb[c] * scale, rtol=1e-9, atol=1e-9 * np.abs(oxb[c]).max() * scale)
+        assert np.allclose(vb[c][idx], ovb[c] * scale, rtol=1e-9, atol=1e-9 * np.abs(ovb[c]).max() * scale)
+    assert np.all(np.isfinite(g))
+    torch.cuda.empty_cache()
