@@ -186,6 +186,21 @@ int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_bytes, void* s
 int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
                       uint32_t** perm);
 
+/* soax_sort_by_cell without a caller workspace.  The paper has no counterpart: this is
+ * for hosts that cannot allocate device memory where they sort -- C or Fortran codes
+ * linking the library with no device allocator of their own, or time-step loops that
+ * forbid cudaMalloc because it can synchronise the device and breaks a memory budget
+ * fixed at start-up.  Same keys, radix sort and permute-gather as soax_sort_by_cell,
+ * with the scratch in a static device array of 22 MiB that every GPU loading the
+ * library holds until exit; this call allocates nothing.  Limits: n <= 1048576 and
+ * grid in 1..64 (SOAX_EINVAL otherwise, before any device work).  perm_out: n u32 on
+ * the device receiving the permutation, or NULL.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (every part is rewritten before use): calls that overlap on the
+ * GPU, on any stream or thread, race and corrupt each other. */
+int soax_sort_by_cell_noalloc(soax_t h, int32_t grid, uint32_t* perm_out, void* stream);
+
 /* ---------------------------------------------------------------- adjoint */
 
 /* Workspace bytes for K steps with a checkpoint every ckpt_every steps. */

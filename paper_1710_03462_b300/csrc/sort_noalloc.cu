@@ -1,0 +1,75 @@
+// soax_sort_by_cell_noalloc: the cell sort for callers that cannot hand the library a
+// device workspace.
+//
+// Some hosts of this library cannot allocate device memory at the point where they want
+// to sort: C or Fortran particle codes that link libsoax directly and have no device
+// allocator of their own, or simulation loops that forbid cudaMalloc between time steps
+// because it may synchronise the whole device and eat into a memory budget fixed at
+// start-up.  This entry point runs the same keys / radix sort / permute-gather as
+// soax_sort_by_cell, with its scratch (keys, sorted keys, permutation, digit counts and
+// the radix ping-pong buffers) in one file-scope device array instead of a caller
+// workspace.  The array is sized for at most kNoAllocMaxParticles particles on a grid of
+// at most kNoAllocMaxGrid cells per side; every GPU that loads the library holds it
+// until the process exits.
+#include <mutex>
+
+#include "soax_internal.h"
+
+namespace {
+
+constexpr int64_t kNoAllocMaxParticles = int64_t(1) << 20;  // 1,048,576 particles
+constexpr int kNoAllocMaxGrid = 64;                         // keys of at most 18 bits
+constexpr size_t kNoAllocScratchBytes = size_t(22) << 20;   // 22 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once with that device current.
+// (In host code the array's name is only a host-side stand-in, never a device address.)
+std::mutex g_noalloc_mu;
+void* g_noalloc_dev_ptr[64] = {};
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return soax::cuda_fail(e, "soax_sort_by_cell_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 64) return soax::fail(SOAX_EUNSUPPORTED, "soax_sort_by_cell_noalloc: device index >= 64");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_dev_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return soax::cuda_fail(e, "soax_sort_by_cell_noalloc: cudaGetSymbolAddress");
+    g_noalloc_dev_ptr[dev] = p;
+  }
+  *out = g_noalloc_dev_ptr[dev];
+  return SOAX_OK;
+}
+
+}  // namespace
+
+extern "C" int soax_sort_by_cell_noalloc(soax_t h, int32_t grid, uint32_t* perm_out, void* stream) {
+  using namespace soax;
+  if (int r = check_handle(h)) return r;
+  if (grid < 1 || grid > kNoAllocMaxGrid)
+    return fail(SOAX_EINVAL, "soax_sort_by_cell_noalloc: grid must be in 1..64 (static scratch limit)");
+  if (h->n > kNoAllocMaxParticles)
+    return fail(SOAX_EINVAL, "soax_sort_by_cell_noalloc: at most 1048576 particles fit the static scratch (n = " +
+                                 std::to_string(h->n) + "); use soax_sort_by_cell with a workspace");
+  size_t need = 0;
+  if (int r = soax_sort_workspace_bytes(h, grid, &need)) return r;
+  if (need > kNoAllocScratchBytes) return fail(SOAX_ENOMEM, "soax_sort_by_cell_noalloc: static scratch too small");
+  if (h->n == 0) return soax_sort_by_cell(h, grid, nullptr, 0, stream);
+  void* ws = nullptr;
+  if (int r = noalloc_scratch(&ws)) return r;
+  // The radix sort clears its per-pass digit totals itself; every other part of the
+  // scratch is fully written before it is read, so nothing left from an earlier call
+  // is used.
+  if (int r = soax_sort_by_cell(h, grid, ws, kNoAllocScratchBytes, stream)) return r;
+  if (perm_out) {
+    uint32_t* perm = nullptr;
+    if (int r = soax_sort_results(h, grid, ws, kNoAllocScratchBytes, nullptr, &perm)) return r;
+    cudaError_t e = cudaMemcpyAsync(perm_out, perm, (size_t)h->n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                    as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "soax_sort_by_cell_noalloc: copy of the permutation");
+  }
+  return SOAX_OK;
+}
