@@ -55,8 +55,11 @@ __device__ __forceinline__ StateRef state_at(char* base, size_t sb, int64_t n, i
 }
 
 __global__ void __launch_bounds__(kAdjBlock) k_adj_forward(EnsArgs e, FlowK f, int K, int C, char* ckpt, size_t sb) {
+  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
+  load_trig_table(s_tab);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= e.n) return;
+  const StepC k = make_stepc(e, f, i);
   double x[3] = {e.px[i], e.py[i], e.pz[i]};
   float v[3] = {e.vx[i], e.vy[i], e.vz[i]}, a[3] = {0.f, 0.f, 0.f};
   for (int s = 0; s < K; ++s) {
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_forward(EnsArgs e, FlowK f, i
         r.v[c][i] = v[c];
       }
     }
-    rk2_step(f, e.inv_tau, x, v, a);
+    rk2_step(k, s_tab, x, v, a);
   }
   e.px[i] = x[0]; e.py[i] = x[1]; e.pz[i] = x[2];
   e.vx[i] = v[0]; e.vy[i] = v[1]; e.vz[i] = v[2];
@@ -98,9 +101,12 @@ __device__ __forceinline__ void block_reduce_fixed(double (&v)[NV], double* out)
 
 __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, int K, int C, int nck, char* ckpt,
                                                           char* stack, size_t sb, AdjIO io, double* partials) {
+  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
+  load_trig_table(s_tab);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double th[4] = {0.0, 0.0, 0.0, 0.0};
   if (i < e.n) {
+    const StepC k = make_stepc(e, f, i);
     double xb[3], vb[3];
     for (int c = 0; c < 3; ++c) {
       xb[c] = io.xbK[c][i];
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, i
           st.x[c][i] = x[c];
           st.v[c][i] = v[c];
         }
-        rk2_step(f, e.inv_tau, x, v, a);
+        rk2_step(k, s_tab, x, v, a);
       }
       for (int j = len - 1; j >= 0; --j) {
         StateRef st = state_at(stack, sb, e.n, j);

@@ -29,8 +29,9 @@ __global__ void __launch_bounds__(512) k_step_batched(const EnsArgs* __restrict_
                                                       const int64_t* __restrict__ prefix, int nens, int64_t ntiles,
                                                       FlowK f, int nsteps_inner) {
   extern __shared__ int64_t s_prefix[];
+  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
   for (int k = threadIdx.x; k <= nens; k += blockDim.x) s_prefix[k] = prefix[k];
-  __syncthreads();
+  load_trig_table(s_tab);
   const int64_t tile_parts = (int64_t)blockDim.x * PPT;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int lo = 0, hi = nens;
@@ -42,9 +43,9 @@ __global__ void __launch_bounds__(512) k_step_batched(const EnsArgs* __restrict_
     const int64_t i0 = (t - s_prefix[lo]) * tile_parts + (int64_t)threadIdx.x * PPT;
     if (i0 < e.n) {
       if (i0 + PPT <= e.n)
-        step_group<PPT, VB>(e, f, i0, nsteps_inner);
+        step_group<PPT, VB>(e, f, s_tab, i0, nsteps_inner);
       else
-        step_tail(e, f, i0, (int)(e.n - i0), nsteps_inner);
+        step_tail(e, f, s_tab, i0, (int)(e.n - i0), nsteps_inner);
     }
   }
 }
@@ -122,7 +123,7 @@ static int prepare(const soax_t* hs, const soax_flow* fls, int nens, const soax_
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (out->smem > 48 * 1024) {
+  if (out->smem > 32 * 1024) {  // plus 16 KB of static shared memory (the sin/cos table)
     cudaError_t e =
         cudaFuncSetAttribute((const void*)out->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return cuda_fail(e, "soax_step_batched: smem attribute");

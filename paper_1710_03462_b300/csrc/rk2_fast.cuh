@@ -1,0 +1,226 @@
+// The midpoint-RK2 step of rk2_native.cuh, evaluated to binary64 accuracy without the
+// FP64 pipe for the trigonometry and the velocity arithmetic.
+//
+// B300 executes FP64 at a small fraction of its FP32 and integer rates (measured: about
+// 1.6 FP64 FMA per SM per clock against ~110 FP32 FMA), and a native binary64 sincos
+// costs ~25 FP64 instructions; the native step is therefore bound by the FP64 pipe at a
+// few percent of HBM bandwidth.  Here:
+//
+//  * real numbers are float-float pairs (hi + lo, ~48 significant bits), built from the
+//    error-free transformations two_sum (Knuth) and two_prod (via FMA), all with
+//    explicitly rounded intrinsics so the compiler cannot contract or reassociate them;
+//  * sin/cos of a position x in [0, 2pi) use an exact fixed-point reduction: x (binary64)
+//    becomes a 64-bit integer X = x 2^61, T = X (4/pi) 2^-63 is frac(x / 2pi) in 2^-64
+//    turns, its top 10 bits select theta_k = 2 pi k / 1024 from a float-float table and
+//    the rest is the residual r = x - theta_k (|r| <= pi/1024) as a float pair; then
+//    sin(theta_k + r) = S + (C sin r + S (cos r - 1)) with short Taylor series for the
+//    residual (a table-driven method in the manner of Tang);
+//  * sin/cos of the midpoint xm = x + (dt/2) v come from those of x by the angle
+//    addition formula with delta = (dt/2) v (|delta| <= ~2e-3);
+//  * the new velocity v + dt a2 is rounded to f32 from the float pair with one IEEE add
+//    (correct rounding of hi + lo); the new position is x + dt vm with vm = vm_hi + vm_lo
+//    applied as two binary64 FMAs (the only FP64 instructions of the step).
+//
+// Accuracy (checked against the CPU oracle by the parity tests): sin/cos to a few 1e-17
+// absolute, velocities before their f32 rounding to ~1e-16 relative, positions within
+// about one binary64 ulp per step of the oracle's.
+#pragma once
+#include <cstdint>
+
+#include "trig_table.inc"
+
+namespace soax {
+
+struct ff {
+  float h, l;  // the value h + l
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// Requires |a| >= |b| or a == 0.
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = two_prod(a.h, b.h);
+  p.l = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l));
+  return p;
+}
+
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  ff p = two_prod(a.h, b);
+  p.l = __fmaf_rn(a.l, b, p.l);
+  return p;
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.h, b.h);
+  s.l = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+  return s;
+}
+
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.h, -b.l}); }
+
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+  ff s = two_sum(a.h, b);
+  s.l = __fadd_rn(s.l, a.l);
+  return s;
+}
+
+// Exact conversion of a binary32 to binary64 with integer instructions (zero and
+// subnormal inputs give a signed zero).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xFFFFFu);
+  uint32_t lo = u << 29;
+  if (e == 0) {
+    hi = u & 0x80000000u;
+    lo = 0;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Per-particle constants of the step, as float pairs.
+struct StepC {
+  ff A, B, C;  // flow amplitudes
+  ff dt, hdt;  // dt and dt/2
+  ff s;        // 1/tau
+  double dt_d; // dt as binary64, for the position update
+};
+
+__device__ __forceinline__ ff ff_from2(const float2 p) { return ff{p.x, p.y}; }
+
+// 1/(ts * m) as a float pair (one Newton step on a correctly rounded float reciprocal).
+__device__ __forceinline__ ff ff_inv_tau(const float2 ts, float m) {
+  const ff t = ff_mul_f(ff_from2(ts), m);
+  const float y0 = __frcp_rn(t.h);
+  const float e = __fsub_rn(__fmaf_rn(-t.h, y0, 1.0f), __fmul_rn(t.l, y0));
+  return fast_two_sum(y0, __fmul_rn(y0, e));
+}
+
+// x (binary64, 0 <= x < 8) -> table index k and residual r = x - 2 pi k / 1024.
+__device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const uint64_t m = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+  const int sh = e - 1014;  // X = x 2^61 = m 2^(e - 1075 + 61)
+  uint64_t X;
+  if (sh >= 0)
+    X = m << sh;  // exact: x >= 2^-8 and x < 8 give 0 <= sh <= 11
+  else
+    X = sh > -64 ? (m >> -sh) : 0ull;  // bits below 2^-61 dropped (< 5e-19)
+  // T = X (4/pi) 2^-63 = frac(x / 2pi) 2^64 (within 3 units of the last place).
+  const uint64_t T = __umul64hi(X, SOAX_FOUR_OVER_PI_2P63) << 1;
+  const uint64_t U = T + (1ull << 53);
+  k = (int)(U >> 54) & (SOAX_TRIG_TABLE_SIZE - 1);
+  // rho = U mod 2^54 = residual + 2^53 in 2^-64 turns, 0 <= rho < 2^54.  Split into
+  // 23-bit pieces and convert each exactly by planting it in a float mantissa.
+  const uint32_t rl = (uint32_t)U, rh = (uint32_t)(U >> 32) & 0x3FFFFFu;
+  const uint32_t c0 = rl & 0x7FFFFFu;
+  const uint32_t c1 = __funnelshift_r(rl, rh, 23) & 0x7FFFFFu;
+  const uint32_t c2 = rh >> 14;
+  const float f0 = __fsub_rn(__uint_as_float(0x4B000000u | c0), 0x1p23f);        // c0
+  const float f1 = __fsub_rn(__uint_as_float(0x56800000u | c1), 0x1p46f);        // c1 2^23
+  const float f2 = __fsub_rn(__uint_as_float(0x62000000u | c2), 0x1.0001p69f);   // c2 2^46 - 2^53
+  const ff q = fast_two_sum(f2, f1);  // |f2| >= 2^46 > f1, or f2 == 0
+  const ff rt = {q.h, __fadd_rn(q.l, f0)};
+  r = ff_mul(rt, ff{SOAX_TWO_PI_2M64_HI, SOAX_TWO_PI_2M64_LO});
+}
+
+// sin and cos of theta_k + r from the table entry (S, C) of theta_k and |r| <= 5e-3.
+__device__ __forceinline__ void sincos_tab(const float4 t, ff r, ff& s, ff& c) {
+  ff p = two_prod(r.h, r.h);  // r^2
+  p.l = __fmaf_rn(__fmul_rn(2.0f, r.h), r.l, p.l);
+  const float p2 = __fmul_rn(p.h, p.h);
+  // cos r - 1 = -r^2/2 + r^4/24 (r^6/720 < 2e-17 dropped)
+  const ff cm = {__fmul_rn(-0.5f, p.h), __fmaf_rn(p2, 1.0f / 24.0f, __fmul_rn(-0.5f, p.l))};
+  // sin r = r + r w, w = -r^2/6 + r^4/120
+  const float wh = __fmul_rn(p.h, -SOAX_SIXTH_HI);
+  float wl = __fmaf_rn(p.h, -SOAX_SIXTH_HI, -wh);
+  wl = __fmaf_rn(p.h, -SOAX_SIXTH_LO, wl);
+  wl = __fmaf_rn(p.l, -SOAX_SIXTH_HI, wl);
+  wl = __fmaf_rn(p2, 1.0f / 120.0f, wl);
+  const ff rw = ff_mul(r, ff{wh, wl});
+  ff sr = fast_two_sum(r.h, rw.h);
+  sr.l = __fadd_rn(sr.l, __fadd_rn(r.l, rw.l));
+  const ff S = {t.x, t.y}, C = {t.z, t.w};
+  s = ff_add(S, ff_add(ff_mul(C, sr), ff_mul(S, cm)));
+  c = ff_add(C, ff_sub(ff_mul(C, cm), ff_mul(S, sr)));
+}
+
+// sin and cos of a + d from those of a, |d| <= ~2e-3.
+__device__ __forceinline__ void sincos_shift(ff sa, ff ca, ff d, ff& s, ff& c) {
+  ff d2 = two_prod(d.h, d.h);
+  d2.l = __fmaf_rn(__fmul_rn(2.0f, d.h), d.l, d2.l);
+  // cos d - 1 = -d^2/2 + d^4/24;  sin d = d - d^3/6 (d^5/120 < 2e-16 relative, dropped)
+  const ff cmd = {__fmul_rn(-0.5f, d2.h), __fmaf_rn(__fmul_rn(d2.h, d2.h), 1.0f / 24.0f, __fmul_rn(-0.5f, d2.l))};
+  const ff sd = {d.h, __fsub_rn(d.l, __fmul_rn(__fmul_rn(d2.h, d.h), 1.0f / 6.0f))};
+  s = ff_add(sa, ff_add(ff_mul(ca, sd), ff_mul(sa, cmd)));
+  c = ff_add(ca, ff_sub(ff_mul(ca, cmd), ff_mul(sa, sd)));
+}
+
+__device__ __forceinline__ double wrap_2pi_fast(double x) {
+  const long long b = __double_as_longlong(x);
+  if (b >= 0x401921FB54442D18ll) return __dsub_rn(x, 6.283185307179586);   // x >= 2pi
+  if (b < 0 && b != (long long)0x8000000000000000ull) return __dadd_rn(x, 6.283185307179586);  // x < 0
+  return x;
+}
+
+// One step: x (binary64 position, in/out), v (f32 velocity, in/out), a2out (the last
+// stage acceleration rounded to f32).  tab: the 1024-entry table (shared memory).
+__device__ __forceinline__ void rk2_step_fast(const StepC& k, const float4* __restrict__ tab, double x[3],
+                                              float v[3], float a2out[3]) {
+  ff s0[3], c0[3], s1[3], c1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    int idx;
+    ff r;
+    reduce_angle(x[c], idx, r);
+    sincos_tab(tab[idx], r, s0[c], c0[c]);
+    sincos_shift(s0[c], c0[c], ff_mul_f(k.hdt, v[c]), s1[c], c1[c]);
+  }
+  // u = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x)
+  const ff u0[3] = {ff_add(ff_mul(k.A, s0[2]), ff_mul(k.C, c0[1])), ff_add(ff_mul(k.B, s0[0]), ff_mul(k.A, c0[2])),
+                    ff_add(ff_mul(k.C, s0[1]), ff_mul(k.B, c0[0]))};
+  const ff u1[3] = {ff_add(ff_mul(k.A, s1[2]), ff_mul(k.C, c1[1])), ff_add(ff_mul(k.B, s1[0]), ff_mul(k.A, c1[2])),
+                    ff_add(ff_mul(k.C, s1[1]), ff_mul(k.B, c1[0]))};
+  float vn[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const ff a1 = ff_mul(ff_add_f(u0[c], -v[c]), k.s);
+    const ff vm = ff_add_f(ff_mul(k.hdt, a1), v[c]);
+    const ff a2 = ff_mul(ff_sub(u1[c], vm), k.s);
+    const ff nv = ff_add_f(ff_mul(k.dt, a2), v[c]);
+    vn[c] = __fadd_rn(nv.h, nv.l);
+    a2out[c] = __fadd_rn(a2.h, a2.l);
+    double xn = __fma_rn(k.dt_d, f2d_exact(vm.h), x[c]);
+    xn = __fma_rn(k.dt_d, f2d_exact(vm.l), xn);
+    x[c] = wrap_2pi_fast(xn);
+  }
+  v[0] = vn[0];
+  v[1] = vn[1];
+  v[2] = vn[2];
+}
+
+static __device__ const float4 kTrigTable[SOAX_TRIG_TABLE_SIZE] = {SOAX_TRIG_TABLE_ENTRIES};
+
+// Copy the table into shared memory (every thread of the block must call this).
+__device__ __forceinline__ void load_trig_table(float4* s_tab) {
+  for (int i = threadIdx.x; i < SOAX_TRIG_TABLE_SIZE; i += blockDim.x) s_tab[i] = kTrigTable[i];
+  __syncthreads();
+}
+
+}  // namespace soax

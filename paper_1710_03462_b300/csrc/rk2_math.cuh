@@ -1,10 +1,12 @@
-// Selects the per-particle step implementation used by every kernel.
+// Selects the per-particle step implementation used by every kernel: the float-float
+// evaluation of rk2_fast.cuh (binary64 accuracy off the FP64 pipe).
 #pragma once
+#include "rk2_fast.cuh"
 #include "rk2_native.cuh"
 
 namespace soax {
-__device__ __forceinline__ void rk2_step(const FlowK& f, double inv_tau, double x[3], float v[3],
+__device__ __forceinline__ void rk2_step(const StepC& k, const float4* __restrict__ tab, double x[3], float v[3],
                                          float a2out[3]) {
-  rk2_step_native(f, inv_tau, x, v, a2out);
+  rk2_step_fast(k, tab, x, v, a2out);
 }
 }  // namespace soax

@@ -21,7 +21,8 @@ namespace soax {
 
 struct FlowK {
   double A, B, C;
-  double dt, hdt;  // hdt = dt/2 (exact)
+  double dt, hdt;     // hdt = dt/2 (exact)
+  float2 dtf, hdtf;   // dt and dt/2 as float pairs (hi, lo)
 };
 
 __device__ __forceinline__ void abc_flow_native(const FlowK& f, const double x[3], double u[3]) {

@@ -62,6 +62,8 @@ inline int grid_for(int64_t work_items, int block) {
 
 struct EnsArgs;
 struct FlowK;
+// Grid of a persistent kernel: resident blocks per SM x SMs, at most work_blocks.
+int persistent_grid(const void* kern, int block, size_t smem, int64_t work_blocks);
 // Validate fl against h's schema and fill the kernel arguments for buffer set buf.
 int make_ens_args(soax_t h, const soax_flow* fl, int buf, EnsArgs* e, FlowK* f, const char* who);
 

@@ -6,6 +6,24 @@
 
 namespace soax {
 
+// d as a float pair: hi = nearest float, lo = nearest float to d - hi.
+float2 split_ff(double d) {
+  const float h = (float)d;
+  return make_float2(h, (float)(d - (double)h));
+}
+
+// Resident blocks per SM of a kernel at the given block size (cached per kernel).
+int persistent_grid(const void* kern, int block, size_t smem, int64_t work_blocks) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  int64_t g = (int64_t)sms * per_sm;
+  if (g > work_blocks) g = work_blocks;
+  return (int)(g < 1 ? 1 : g);
+}
+
 int make_ens_args(soax_t h, const soax_flow* fl, int buf, EnsArgs* e, FlowK* f, const char* who) {
   std::string w(who);
   if (!fl) return fail(SOAX_EINVAL, w + ": flow is NULL");
@@ -47,6 +65,11 @@ int make_ens_args(soax_t h, const soax_flow* fl, int buf, EnsArgs* e, FlowK* f, 
   e->C = fl->C;
   e->inv_tau = fl->tau_field >= 0 ? 0.0 : 1.0 / fl->tau;
   e->tau_scale = fl->tau_scale;
+  e->Af = split_ff(fl->A);
+  e->Bf = split_ff(fl->B);
+  e->Cf = split_ff(fl->C);
+  e->itf = split_ff(e->inv_tau);
+  e->tsf = split_ff(fl->tau_scale);
   if (h->n > 0) {
     if (!e->px || !e->py || !e->pz || !e->vx || !e->vy || !e->vz ||
         (fl->acc_field >= 0 && (!e->ax || !e->ay || !e->az)) || (fl->tau_field >= 0 && !e->tau_src))
@@ -57,41 +80,56 @@ int make_ens_args(soax_t h, const soax_flow* fl, int buf, EnsArgs* e, FlowK* f, 
   f->C = fl->C;
   f->dt = fl->dt;
   f->hdt = 0.5 * fl->dt;
+  f->dtf = split_ff(f->dt);
+  f->hdtf = split_ff(f->hdt);
   return SOAX_OK;
 }
 
-constexpr int kStepPPT = 4;
-constexpr int kStepBlock = 256;
+// Launch shape of the plain step, picked by timing every batched shape on 16.7M particles.
+constexpr int kStepPPT = 2;
+constexpr int kStepBlock = 512;
 
+// Persistent: a grid that fills the GPU once walks groups of PPT particles with a
+// fixed stride, so each block copies the sin/cos table into shared memory only once.
 template <int PPT, int VB>
 __global__ void __launch_bounds__(kStepBlock) k_step_soa(EnsArgs e, FlowK f) {
-  int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * PPT;
-  if (i0 >= e.n) return;
-  if (i0 + PPT <= e.n)
-    step_group<PPT, VB>(e, f, i0, 1);
-  else
-    step_tail(e, f, i0, (int)(e.n - i0), 1);
+  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
+  load_trig_table(s_tab);
+  const int64_t ngroups = (e.n + PPT - 1) / PPT;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = g * PPT;
+    if (i0 + PPT <= e.n)
+      step_group<PPT, VB>(e, f, s_tab, i0, 1);
+    else
+      step_tail(e, f, s_tab, i0, (int)(e.n - i0), 1);
+  }
 }
 
 struct AosArgs {
   char* rec;
   int64_t R, pos_off, vel_off, acc_off, tau_off;  // offsets in bytes; -1 = absent
   int64_t n;
-  double A, B, C, inv_tau, tau_scale;
+  EnsArgs e;  // flow amplitudes and tau (the plane pointers are unused)
 };
 
-__global__ void __launch_bounds__(256) k_step_aos(AosArgs a, FlowK fdt) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const FlowK f{a.A, a.B, a.C, fdt.dt, fdt.hdt};
+__global__ void __launch_bounds__(256) k_step_aos(AosArgs a, FlowK f) {
+  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
+  load_trig_table(s_tab);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
   char* r = a.rec + i * a.R;
   const double* pp = reinterpret_cast<const double*>(r + a.pos_off);
   const float* vp = reinterpret_cast<const float*>(r + a.vel_off);
   double p[3] = {pp[0], pp[1], pp[2]};
   float v[3] = {vp[0], vp[1], vp[2]}, acc[3];
-  double it = a.inv_tau;
-  if (a.tau_off >= 0) it = 1.0 / __dmul_rn(a.tau_scale, (double)*reinterpret_cast<const float*>(r + a.tau_off));
-  rk2_step(f, it, p, v, acc);
+  StepC k;
+  k.A = ff_from2(a.e.Af);
+  k.B = ff_from2(a.e.Bf);
+  k.C = ff_from2(a.e.Cf);
+  k.dt = ff_from2(f.dtf);
+  k.hdt = ff_from2(f.hdtf);
+  k.dt_d = f.dt;
+  k.s = a.tau_off >= 0 ? ff_inv_tau(a.e.tsf, *reinterpret_cast<const float*>(r + a.tau_off)) : ff_from2(a.e.itf);
+  rk2_step(k, s_tab, p, v, acc);
   double* pw = reinterpret_cast<double*>(r + a.pos_off);
   float* vw = reinterpret_cast<float*>(r + a.vel_off);
   pw[0] = p[0]; pw[1] = p[1]; pw[2] = p[2];
@@ -99,6 +137,7 @@ __global__ void __launch_bounds__(256) k_step_aos(AosArgs a, FlowK fdt) {
   if (a.acc_off >= 0) {
     float* aw = reinterpret_cast<float*>(r + a.acc_off);
     aw[0] = acc[0]; aw[1] = acc[1]; aw[2] = acc[2];
+  }
   }
 }
 
@@ -113,7 +152,8 @@ extern "C" int soax_step(soax_t h, const soax_flow* fl, int32_t nsteps, void* st
   FlowK f;
   if (int r = make_ens_args(h, fl, h->current, &e, &f, "soax_step")) return r;
   if (h->n == 0 || nsteps == 0) return SOAX_OK;
-  int grid = grid_for((h->n + kStepPPT - 1) / kStepPPT, kStepBlock);
+  const int grid = persistent_grid((const void*)k_step_soa<kStepPPT, 128>, kStepBlock, 0,
+                                   grid_for((h->n + kStepPPT - 1) / kStepPPT, kStepBlock));
   cudaStream_t s = as_stream(stream);
   for (int k = 0; k < nsteps; ++k) {
     k_step_soa<kStepPPT, 128><<<grid, kStepBlock, 0, s>>>(e, f);
@@ -142,14 +182,11 @@ extern "C" int soax_step_aos(soax_t h, void* aos_dev, const soax_flow* fl, int32
   a.acc_off = fl->acc_field >= 0 ? h->offsets[fl->acc_field] : -1;
   a.tau_off = fl->tau_field >= 0 ? h->offsets[fl->tau_field] : -1;
   a.n = h->n;
-  a.A = e.A;
-  a.B = e.B;
-  a.C = e.C;
-  a.inv_tau = e.inv_tau;
-  a.tau_scale = e.tau_scale;
+  a.e = e;
+  const int grid = persistent_grid((const void*)k_step_aos, 256, 0, grid_for(h->n, 256));
   // One pass over the records per step, like soax_step.
   for (int k = 0; k < nsteps; ++k) {
-    k_step_aos<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(a, f);
+    k_step_aos<<<grid, 256, 0, as_stream(stream)>>>(a, f);
     if (int r = check_launch("soax_step_aos")) return r;
   }
   return SOAX_OK;

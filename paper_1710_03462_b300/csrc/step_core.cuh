@@ -25,7 +25,21 @@ struct EnsArgs {
   double A, B, C;
   double inv_tau;    // 1/tau when tau_src is null
   double tau_scale;  // tau_i = tau_scale * tau_src[i] otherwise
+  float2 Af, Bf, Cf, itf, tsf;  // A, B, C, inv_tau, tau_scale as float pairs (hi, lo)
 };
+
+// The step constants of particle i of ensemble e (dt from f).
+__device__ __forceinline__ StepC make_stepc(const EnsArgs& e, const FlowK& f, int64_t i) {
+  StepC c;
+  c.A = ff_from2(e.Af);
+  c.B = ff_from2(e.Bf);
+  c.C = ff_from2(e.Cf);
+  c.dt = ff_from2(f.dtf);
+  c.hdt = ff_from2(f.hdtf);
+  c.dt_d = f.dt;
+  c.s = e.tau_src ? ff_inv_tau(e.tsf, e.tau_src[i]) : ff_from2(e.itf);
+  return c;
+}
 
 template <int PPT, int VB>
 __device__ __forceinline__ void load_f64(const double* __restrict__ p, int64_t i0, double (&o)[PPT]) {
@@ -86,16 +100,12 @@ __device__ __forceinline__ void store_f32(float* __restrict__ p, int64_t i0, con
   }
 }
 
-__device__ __forceinline__ double particle_inv_tau(const EnsArgs& e, int64_t i) {
-  if (e.tau_src) return 1.0 / __dmul_rn(e.tau_scale, (double)e.tau_src[i]);
-  return e.inv_tau;
-}
-
 // Advance the PPT particles i0..i0+PPT-1 (all < n) by nsteps steps, one load and one
-// store of each plane.  The flow amplitudes come from e; fdt supplies dt and dt/2.
+// store of each plane.  The flow amplitudes and tau come from e; f supplies dt and dt/2;
+// tab is the sin/cos table in shared memory.
 template <int PPT, int VB>
-__device__ __forceinline__ void step_group(const EnsArgs& e, const FlowK& fdt, int64_t i0, int nsteps) {
-  const FlowK f{e.A, e.B, e.C, fdt.dt, fdt.hdt};
+__device__ __forceinline__ void step_group(const EnsArgs& e, const FlowK& f, const float4* tab, int64_t i0,
+                                           int nsteps) {
   double x[PPT], y[PPT], z[PPT];
   float vx[PPT], vy[PPT], vz[PPT];
   load_f64<PPT, VB>(e.px, i0, x);
@@ -104,16 +114,14 @@ __device__ __forceinline__ void step_group(const EnsArgs& e, const FlowK& fdt, i
   load_f32<PPT, VB>(e.vx, i0, vx);
   load_f32<PPT, VB>(e.vy, i0, vy);
   load_f32<PPT, VB>(e.vz, i0, vz);
-  double it[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) it[j] = particle_inv_tau(e, i0 + j);
   float ax[PPT], ay[PPT], az[PPT];
-  for (int s = 0; s < nsteps; ++s) {
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) {
+  for (int j = 0; j < PPT; ++j) {
+    const StepC k = make_stepc(e, f, i0 + j);
+    for (int s = 0; s < nsteps; ++s) {
       double p[3] = {x[j], y[j], z[j]};
       float v[3] = {vx[j], vy[j], vz[j]}, a[3];
-      rk2_step(f, it[j], p, v, a);
+      rk2_step(k, tab, p, v, a);
       x[j] = p[0]; y[j] = p[1]; z[j] = p[2];
       vx[j] = v[0]; vy[j] = v[1]; vz[j] = v[2];
       ax[j] = a[0]; ay[j] = a[1]; az[j] = a[2];
@@ -133,14 +141,14 @@ __device__ __forceinline__ void step_group(const EnsArgs& e, const FlowK& fdt, i
 }
 
 // Scalar path for the ragged tail: particles i0..i0+cnt-1.
-__device__ __forceinline__ void step_tail(const EnsArgs& e, const FlowK& fdt, int64_t i0, int cnt, int nsteps) {
-  const FlowK f{e.A, e.B, e.C, fdt.dt, fdt.hdt};
+__device__ __forceinline__ void step_tail(const EnsArgs& e, const FlowK& f, const float4* tab, int64_t i0, int cnt,
+                                          int nsteps) {
   for (int j = 0; j < cnt; ++j) {
     int64_t i = i0 + j;
     double p[3] = {e.px[i], e.py[i], e.pz[i]};
     float v[3] = {e.vx[i], e.vy[i], e.vz[i]}, a[3] = {0.f, 0.f, 0.f};
-    double it = particle_inv_tau(e, i);
-    for (int s = 0; s < nsteps; ++s) rk2_step(f, it, p, v, a);
+    const StepC k = make_stepc(e, f, i);
+    for (int s = 0; s < nsteps; ++s) rk2_step(k, tab, p, v, a);
     e.px[i] = p[0]; e.py[i] = p[1]; e.pz[i] = p[2];
     e.vx[i] = v[0]; e.vy[i] = v[1]; e.vz[i] = v[2];
     if (e.ax && nsteps > 0) { e.ax[i] = a[0]; e.ay[i] = a[1]; e.az[i] = a[2]; }
