@@ -77,6 +77,13 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_forward(EnsArgs e, FlowK f, i
   if (e.ax && K > 0) { e.ax[i] = a[0]; e.ay[i] = a[1]; e.az[i] = a[2]; }
 }
 
+// binary64 <-> float pair (once per particle, outside the step loop).
+__device__ __forceinline__ ff d2ff(double d) {
+  const float h = __double2float_rn(d);
+  return ff{h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double ff2d(ff a) { return (double)a.h + (double)a.l; }
+
 struct AdjIO {
   const double* xbK[3];
   const double* vbK[3];  // all null: zero
@@ -107,10 +114,10 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, i
   double th[4] = {0.0, 0.0, 0.0, 0.0};
   if (i < e.n) {
     const StepC k = make_stepc(e, f, i);
-    double xb[3], vb[3];
+    ff xb[3], vb[3], tf[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int c = 0; c < 3; ++c) {
-      xb[c] = io.xbK[c][i];
-      vb[c] = io.vbK[0] ? io.vbK[c][i] : 0.0;
+      xb[c] = d2ff(io.xbK[c][i]);
+      vb[c] = io.vbK[0] ? d2ff(io.vbK[c][i]) : ff{0.f, 0.f};
     }
     float a[3];
     for (int seg = nck - 1; seg >= 0; --seg) {
@@ -136,13 +143,14 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, i
           x[c] = st.x[c][i];
           v[c] = st.v[c][i];
         }
-        rk2_reverse_native(f, e.inv_tau, x, v, xb, vb, th);
+        rk2_reverse_fast(k, s_tab, x, v, xb, vb, tf);
       }
     }
     for (int c = 0; c < 3; ++c) {
-      io.xb0[c][i] = xb[c];
-      io.vb0[c][i] = vb[c];
+      io.xb0[c][i] = ff2d(xb[c]);
+      io.vb0[c][i] = ff2d(vb[c]);
     }
+    for (int c = 0; c < 4; ++c) th[c] = ff2d(tf[c]);
   }
   block_reduce_fixed<4, kAdjBlock>(th, partials + 4 * (size_t)blockIdx.x);
 }

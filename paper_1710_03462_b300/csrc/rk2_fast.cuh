@@ -1,5 +1,14 @@
-// The midpoint-RK2 step of rk2_native.cuh, evaluated to binary64 accuracy without the
-// FP64 pipe for the trigonometry and the velocity arithmetic.
+// Per-particle midpoint-RK2 step of an inertial particle in the ABC flow, and its
+// reverse-mode derivative:
+//
+//   u(x)   = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x)
+//   a1     = (u(x) - v) / tau,      xm = x + (dt/2) v,      vm = v + (dt/2) a1
+//   a2     = (u(xm) - vm) / tau
+//   x'     = x + dt vm, wrapped once into [0, 2pi);   v' = v + dt a2, rounded to f32
+//
+// (the Euler advection x += dt*v of Eq. 1, Sec. 2, generalised to inertial particles),
+// evaluated to binary64 accuracy without the FP64 pipe for the trigonometry and the
+// velocity arithmetic.
 //
 // B300 executes FP64 at a small fraction of its FP32 and integer rates (measured: about
 // 1.6 FP64 FMA per SM per clock against ~110 FP32 FMA), and a native binary64 sincos
@@ -21,15 +30,25 @@
 //    (correct rounding of hi + lo); the new position is x + dt vm with vm = vm_hi + vm_lo
 //    applied as two binary64 FMAs (the only FP64 instructions of the step).
 //
-// Accuracy (checked against the CPU oracle by the parity tests): sin/cos to a few 1e-17
-// absolute, velocities before their f32 rounding to ~1e-16 relative, positions within
-// about one binary64 ulp per step of the oracle's.
+// Accuracy (checked against the CPU oracle by the parity tests): sin/cos to ~4e-15
+// absolute (the 2^-48 precision of a float pair); the flow enters v' scaled by
+// dt/tau <= 0.1, so velocities before their f32 rounding are within ~1e-16 relative of
+// binary64 arithmetic, and positions within about one binary64 ulp per step.
 #pragma once
 #include <cstdint>
 
 #include "trig_table.inc"
 
 namespace soax {
+
+#define SOAX_TWO_PI 6.283185307179586  // binary64 nearest to 2pi (0x401921FB54442D18)
+
+// Step parameters shared by every particle of a launch.
+struct FlowK {
+  double A, B, C;
+  double dt, hdt;     // hdt = dt/2 (exact)
+  float2 dtf, hdtf;   // dt and dt/2 as float pairs (hi, lo)
+};
 
 struct ff {
   float h, l;  // the value h + l
@@ -179,11 +198,9 @@ __device__ __forceinline__ double wrap_2pi_fast(double x) {
   return x;
 }
 
-// One step: x (binary64 position, in/out), v (f32 velocity, in/out), a2out (the last
-// stage acceleration rounded to f32).  tab: the 1024-entry table (shared memory).
-__device__ __forceinline__ void rk2_step_fast(const StepC& k, const float4* __restrict__ tab, double x[3],
-                                              float v[3], float a2out[3]) {
-  ff s0[3], c0[3], s1[3], c1[3];
+// sin and cos of the three coordinates of x (s0, c0) and of xm = x + (dt/2) v (s1, c1).
+__device__ __forceinline__ void step_trig(const StepC& k, const float4* __restrict__ tab, const double x[3],
+                                          const float v[3], ff s0[3], ff c0[3], ff s1[3], ff c1[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     int idx;
@@ -192,11 +209,23 @@ __device__ __forceinline__ void rk2_step_fast(const StepC& k, const float4* __re
     sincos_tab(tab[idx], r, s0[c], c0[c]);
     sincos_shift(s0[c], c0[c], ff_mul_f(k.hdt, v[c]), s1[c], c1[c]);
   }
-  // u = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x)
-  const ff u0[3] = {ff_add(ff_mul(k.A, s0[2]), ff_mul(k.C, c0[1])), ff_add(ff_mul(k.B, s0[0]), ff_mul(k.A, c0[2])),
-                    ff_add(ff_mul(k.C, s0[1]), ff_mul(k.B, c0[0]))};
-  const ff u1[3] = {ff_add(ff_mul(k.A, s1[2]), ff_mul(k.C, c1[1])), ff_add(ff_mul(k.B, s1[0]), ff_mul(k.A, c1[2])),
-                    ff_add(ff_mul(k.C, s1[1]), ff_mul(k.B, c1[0]))};
+}
+
+// u = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x) from the sines and cosines.
+__device__ __forceinline__ void abc_u(const StepC& k, const ff s[3], const ff c[3], ff u[3]) {
+  u[0] = ff_add(ff_mul(k.A, s[2]), ff_mul(k.C, c[1]));
+  u[1] = ff_add(ff_mul(k.B, s[0]), ff_mul(k.A, c[2]));
+  u[2] = ff_add(ff_mul(k.C, s[1]), ff_mul(k.B, c[0]));
+}
+
+// One step: x (binary64 position, in/out), v (f32 velocity, in/out), a2out (the last
+// stage acceleration rounded to f32).  tab: the 1024-entry table (shared memory).
+__device__ __forceinline__ void rk2_step_fast(const StepC& k, const float4* __restrict__ tab, double x[3],
+                                              float v[3], float a2out[3]) {
+  ff s0[3], c0[3], s1[3], c1[3], u0[3], u1[3];
+  step_trig(k, tab, x, v, s0, c0, s1, c1);
+  abc_u(k, s0, c0, u0);
+  abc_u(k, s1, c1, u1);
   float vn[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -213,6 +242,69 @@ __device__ __forceinline__ void rk2_step_fast(const StepC& k, const float4* __re
   v[0] = vn[0];
   v[1] = vn[1];
   v[2] = vn[2];
+}
+
+// xb += J(x)^T ub and th[0..2] += (du/d(A, B, C))^T ub at the point whose sines and
+// cosines are s, c:  J = [[0, -C sin y, A cos z], [B cos x, 0, -A sin z],
+// [-B sin x, C cos y, 0]],  du/dA = (sin z, cos z, 0), du/dB = (0, sin x, cos x),
+// du/dC = (cos y, 0, sin y).
+__device__ __forceinline__ void abc_vjp(const StepC& k, const ff s[3], const ff c[3], const ff ub[3], ff xb[3],
+                                        ff th[4]) {
+  const ff gA = ff_add(ff_mul(s[2], ub[0]), ff_mul(c[2], ub[1]));  // du/dA . ub
+  const ff gB = ff_add(ff_mul(s[0], ub[1]), ff_mul(c[0], ub[2]));
+  const ff gC = ff_add(ff_mul(c[1], ub[0]), ff_mul(s[1], ub[2]));
+  th[0] = ff_add(th[0], gA);
+  th[1] = ff_add(th[1], gB);
+  th[2] = ff_add(th[2], gC);
+  xb[0] = ff_add(xb[0], ff_mul(k.B, ff_sub(ff_mul(c[0], ub[1]), ff_mul(s[0], ub[2]))));
+  xb[1] = ff_add(xb[1], ff_mul(k.C, ff_sub(ff_mul(c[1], ub[2]), ff_mul(s[1], ub[0]))));
+  xb[2] = ff_add(xb[2], ff_mul(k.A, ff_sub(ff_mul(c[2], ub[0]), ff_mul(s[2], ub[1]))));
+}
+
+// Reverse of one step: given the adjoints (xb, vb) of (x', v'), overwrite them with the
+// adjoints of (x, v) and accumulate d/d(A, B, C, tau) into th.  (x, v) is the state
+// before the step.  The f32 rounding of v' and the periodic wrap are differentiated as
+// the identity.  Reverse-mode differentiation of rk2_step_fast's statements, last first:
+//   x' = x + dt vm:       xb += xb',  vmb = dt xb'
+//   v' = v + dt a2:       vb += vb',  a2b = dt vb'
+//   a2 = (u(xm) - vm) s:  u1b = s a2b,  vmb -= s a2b,  sb += a2b . (u1 - vm)
+//   u1 = u(xm):           xmb = J(xm)^T u1b,  thb += (du/dtheta)(xm)^T u1b
+//   vm = v + dt/2 a1:     vb += vmb,  a1b = dt/2 vmb
+//   xm = x + dt/2 v:      xb += xmb,  vb += dt/2 xmb
+//   a1 = (u(x) - v) s:    u0b = s a1b,  vb -= s a1b,  sb += a1b . (u0 - v)
+//   u0 = u(x):            xb += J(x)^T u0b,  thb += (du/dtheta)(x)^T u0b
+//   s = 1/tau:            taub = -s^2 sb
+__device__ __forceinline__ void rk2_reverse_fast(const StepC& k, const float4* __restrict__ tab, const double x[3],
+                                                 const float v[3], ff xb[3], ff vb[3], ff th[4]) {
+  ff s0[3], c0[3], s1[3], c1[3], u0[3], u1[3];
+  step_trig(k, tab, x, v, s0, c0, s1, c1);
+  abc_u(k, s0, c0, u0);
+  abc_u(k, s1, c1, u1);
+  ff d0[3], d1[3], u1b[3], vmb[3], xmb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  ff sb = {0.f, 0.f};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    d0[c] = ff_add_f(u0[c], -v[c]);  // u0 - v
+    const ff a1 = ff_mul(d0[c], k.s);
+    const ff vm = ff_add_f(ff_mul(k.hdt, a1), v[c]);
+    d1[c] = ff_sub(u1[c], vm);  // u1 - vm
+    const ff a2b = ff_mul(k.dt, vb[c]);
+    u1b[c] = ff_mul(k.s, a2b);
+    vmb[c] = ff_sub(ff_mul(k.dt, xb[c]), u1b[c]);
+    sb = ff_add(sb, ff_mul(a2b, d1[c]));
+  }
+  abc_vjp(k, s1, c1, u1b, xmb, th);
+  ff u0b[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const ff a1b = ff_mul(k.hdt, vmb[c]);
+    u0b[c] = ff_mul(k.s, a1b);
+    vb[c] = ff_sub(ff_add(vb[c], ff_add(vmb[c], ff_mul(k.hdt, xmb[c]))), u0b[c]);
+    xb[c] = ff_add(xb[c], xmb[c]);
+    sb = ff_add(sb, ff_mul(a1b, d0[c]));
+  }
+  abc_vjp(k, s0, c0, u0b, xb, th);
+  th[3] = ff_sub(th[3], ff_mul(ff_mul(k.s, k.s), sb));
 }
 
 static __device__ const float4 kTrigTable[SOAX_TRIG_TABLE_SIZE] = {SOAX_TRIG_TABLE_ENTRIES};

@@ -2,7 +2,6 @@
 // evaluation of rk2_fast.cuh (binary64 accuracy off the FP64 pipe).
 #pragma once
 #include "rk2_fast.cuh"
-#include "rk2_native.cuh"
 
 namespace soax {
 __device__ __forceinline__ void rk2_step(const StepC& k, const float4* __restrict__ tab, double x[3], float v[3],
