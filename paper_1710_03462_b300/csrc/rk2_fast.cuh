@@ -92,6 +92,13 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.h, -b.l}); }
 
+// a + b when |a.h| >= |b.h| or a.h == 0 (Dekker's fast two-sum on the high parts).
+__device__ __forceinline__ ff ff_add_ordered(ff a, ff b) {
+  ff s = fast_two_sum(a.h, b.h);
+  s.l = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+  return s;
+}
+
 __device__ __forceinline__ ff ff_add_f(ff a, float b) {
   ff s = two_sum(a.h, b);
   s.l = __fadd_rn(s.l, a.l);
@@ -175,9 +182,13 @@ __device__ __forceinline__ void sincos_tab(const float4 t, ff r, ff& s, ff& c) {
   const ff rw = ff_mul(r, ff{wh, wl});
   ff sr = fast_two_sum(r.h, rw.h);
   sr.l = __fadd_rn(sr.l, __fadd_rn(r.l, rw.l));
+  // Every table entry is 0 or at least sin(2pi/1024) = 6.1e-3 in magnitude while
+  // |r| <= pi/1024 = 3.1e-3, so in each sum below the first term is zero or the larger
+  // one: |S|, |C| > |C sr|, |S sr| >= 6.1e-3 |r| > r^2/2 >= |S cm|, |C cm|.
   const ff S = {t.x, t.y}, C = {t.z, t.w};
-  s = ff_add(S, ff_add(ff_mul(C, sr), ff_mul(S, cm)));
-  c = ff_add(C, ff_sub(ff_mul(C, cm), ff_mul(S, sr)));
+  const ff Ssr = ff_mul(S, sr), Csr = ff_mul(C, sr);
+  s = ff_add_ordered(S, ff_add_ordered(Csr, ff_mul(S, cm)));
+  c = ff_add_ordered(C, ff_add_ordered(ff{-Ssr.h, -Ssr.l}, ff_mul(C, cm)));
 }
 
 // sin and cos of a + d from those of a, |d| <= ~2e-3.

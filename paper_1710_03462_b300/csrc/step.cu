@@ -85,14 +85,16 @@ int make_ens_args(soax_t h, const soax_flow* fl, int buf, EnsArgs* e, FlowK* f, 
   return SOAX_OK;
 }
 
-// Launch shape of the plain step, picked by timing every batched shape on 16.7M particles.
+// Launch shape of the plain step, picked by timing launch shapes on 16.7M particles:
+// 2 particles per thread, 512 threads, 2 resident blocks per SM (64 registers).
 constexpr int kStepPPT = 2;
 constexpr int kStepBlock = 512;
+constexpr int kStepMinBlocks = 2;
 
 // Persistent: a grid that fills the GPU once walks groups of PPT particles with a
 // fixed stride, so each block copies the sin/cos table into shared memory only once.
 template <int PPT, int VB>
-__global__ void __launch_bounds__(kStepBlock) k_step_soa(EnsArgs e, FlowK f) {
+__global__ void __launch_bounds__(kStepBlock, kStepMinBlocks) k_step_soa(EnsArgs e, FlowK f) {
   __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
   load_trig_table(s_tab);
   const int64_t ngroups = (e.n + PPT - 1) / PPT;
