@@ -11,6 +11,8 @@
 // scan); (3) every block ranks its tile stably (warp match + per-warp counters, in tile
 // order), stages the tile in shared memory in digit order and writes each digit's run
 // contiguously.  No block waits on another block, so nothing can hang.
+#include <cstring>
+
 #include "soax_internal.h"
 
 namespace soax {
@@ -85,14 +87,35 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
 }
 
 // ------------------------------------------------------------------ cell keys
+// floor(RN(x * c)) for 0 <= x and 0 < c with x * c < 2^31, computed exactly with integer
+// instructions (the binary64 product rounded to nearest-even, then truncated), so the
+// result equals (int)(x * c) of IEEE binary64 arithmetic without using the FP64 pipe.
+// cm: c's 53-bit significand; ce: c's biased exponent.
+__device__ __forceinline__ int floor_mul_rn(double x, uint64_t cm, int ce) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0 || (b >> 63)) return 0;  // zero, subnormal or negative: the product truncates to 0
+  const uint64_t mx = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  // M = mx * cm, 105 or 106 bits; x c = M 2^(ex + ce - 2150).
+  const uint64_t hi = __umul64hi(mx, cm), lo = mx * cm;
+  const int d = (hi >> 41) ? 53 : 52;  // bits to drop to keep 53 significant bits
+  uint64_t mr = (hi << (64 - d)) | (lo >> d);
+  const uint64_t rem = lo & ((1ull << d) - 1), half = 1ull << (d - 1);
+  if (rem > half || (rem == half && (mr & 1))) ++mr;  // round to nearest, ties to even
+  const int t = 2150 - ex - ce - d;  // RN(x c) = mr 2^-t
+  if (t >= 64) return 0;
+  if (t <= 0) return 0x7FFFFFFF;  // outside the key range (clamped by the caller)
+  return (int)(mr >> t);
+}
+
 __global__ void __launch_bounds__(256) k_cell_keys(const double* __restrict__ px, const double* __restrict__ py,
-                                                   const double* __restrict__ pz, int64_t n, double c, int G,
-                                                   uint32_t* __restrict__ keys) {
+                                                   const double* __restrict__ pz, int64_t n, uint64_t cm, int ce,
+                                                   int G, uint32_t* __restrict__ keys) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int ix = min(__double2int_rz(__dmul_rn(px[i], c)), G - 1);
-  int iy = min(__double2int_rz(__dmul_rn(py[i], c)), G - 1);
-  int iz = min(__double2int_rz(__dmul_rn(pz[i], c)), G - 1);
+  int ix = min(floor_mul_rn(px[i], cm, ce), G - 1);
+  int iy = min(floor_mul_rn(py[i], cm, ce), G - 1);
+  int iz = min(floor_mul_rn(pz[i], cm, ce), G - 1);
   keys[i] = (uint32_t)((iz * G + iy) * G + ix);
 }
 
@@ -148,7 +171,7 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scan_rows(uint32_t* __re
   }
 }
 
-__global__ void __launch_bounds__(kSortBlock) k_radix_downsweep(
+__global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n, int shift, uint32_t mask, int64_t nblocks,
     const uint32_t* __restrict__ counts) {
@@ -327,7 +350,11 @@ extern "C" int soax_cell_keys(soax_t h, int32_t pos_field, int32_t grid, uint32_
   const double* pz = (const double*)h->planes[h->current][fp + 2];
   if (!px || !py || !pz) return fail(SOAX_EUNBOUND, "soax_cell_keys: position planes not bound");
   const double c = (double)grid / SOAX_TWO_PI_HOST;
-  k_cell_keys<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n, c, grid, keys);
+  uint64_t cb;
+  std::memcpy(&cb, &c, sizeof cb);
+  const uint64_t cm = (cb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int ce = (int)((cb >> 52) & 0x7FF);
+  k_cell_keys<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n, cm, ce, grid, keys);
   return check_launch("soax_cell_keys");
 }
 
@@ -358,6 +385,10 @@ extern "C" int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* va
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     cudaError_t e = cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)downsweep_smem(kMaxRadix));
+    // Prefer shared memory over L1 so that three 53 KB blocks fit on an SM.
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: smem attribute");
     attr_set[dev] = true;
   }

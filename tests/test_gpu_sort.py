@@ -122,3 +122,24 @@ def test_full_size_wide_n64M_sort():
             assert np.array_equal(a, b[pi]), name
     del p, g
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("G", [32, 64, 1000])
+def test_cell_keys_near_every_boundary(G):
+    """Positions within a few ulps of every cell boundary: the product x * (G/2pi) must
+    round (then truncate) exactly as binary64 arithmetic does."""
+    c = G / sx.TWO_PI
+    base = np.arange(G + 1) / c
+    xs = [base]
+    up, dn = base.copy(), base.copy()
+    for _ in range(6):
+        up = np.nextafter(up, np.inf)
+        dn = np.nextafter(dn, -np.inf)
+        xs += [up.copy(), dn.copy()]
+    x = np.concatenate(xs)
+    x = x[(x >= 0) & (x < sx.TWO_PI)]
+    rng = np.random.default_rng(G)
+    pos = [np.ascontiguousarray(rng.permutation(x)) for _ in range(3)]
+    p = sx.Particles([("pos", "f64", 3, "P")], x.size)
+    p.load({"pos": pos})
+    assert np.array_equal(_u32(p.cell_keys(G)), oracle.cell_keys(*pos, G))
