@@ -343,10 +343,38 @@ def _time(torch, fn, reps=1):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
+def euler_replica(sx, torch, n, dev):
+    """The paper's experiment on B300 (Sec. 2-3): Eq. 1 in single precision on SoA planes
+    (fused; and one launch per component, as the paper's GPU code) and on Listing 4's
+    AoS_SIZE records; time per particle and the AoS/SoA ratios the paper reports."""
+    rng = np.random.default_rng(1)
+    out = {"n": n, "algorithmic_bytes_per_particle": 36}
+    q = sx.Particles([("x", "f32", 3, "P"), ("v", "f32", 3, "V")], n, device=dev, shadow=False)
+    for name in ("x", "v"):
+        for t in q.field(name):
+            t.normal_()
+    t_fused = _time(torch, lambda: q.euler(1e-3), reps=10)
+    t_comp = _time(torch, lambda: q.euler(1e-3, per_component=True), reps=10)
+    out["soa_fused_ns_per_particle"] = t_fused / n * 1e9
+    out["soa_fused_GB/s"] = 36 * n / t_fused / 1e9
+    out["soa_per_component_ns_per_particle"] = t_comp / n * 1e9
+    del q
+    for size in (0, 32):
+        rb = 24 + 4 * size
+        rec = torch.empty(n * rb // 4, dtype=torch.float32, device=dev).normal_()
+        t_aos = _time(torch, lambda: sx.euler_aos(rec, n, rb, 0, 12, 1e-3), reps=10)
+        out[f"aos{size}_ns_per_particle"] = t_aos / n * 1e9
+        out[f"aos{size}_over_soa_per_component"] = t_aos / t_comp
+        del rec
+    torch.cuda.empty_cache()
+    return out
+
+
 def secondary_rows(sx, torch, p, d, dev):
     rows = {}
     n = p.n
     flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
+    rows["euler_replica"] = euler_replica(sx, torch, n, dev)
     # AoS <-> SoA round trip (176 algorithmic bytes per particle) and the AoS step (96).
     aos = p.to_aos()
     t_rt = _time(torch, lambda: (p.to_aos(aos), p.from_aos(aos)), reps=5)

@@ -132,7 +132,7 @@ int soax_aos_layout(soax_t h, int64_t* record_bytes, int64_t* field_offsets);
 
 /* Bulk getElement (Listing 6, Sec. 4.1): copy n AoS records (layout from
  * soax_aos_layout, 16-byte aligned device buffer) into the live planes, byte for byte;
- * padding bytes are ignored. */
+ * padding bytes are ignored.  Records of up to 400 bytes (SOAX_EUNSUPPORTED beyond). */
 int soax_aos_to_soa(soax_t h, const void* aos_dev, void* stream);
 
 /* Bulk push_back (Listing 6): copy the live planes into n AoS records, byte for byte,
@@ -200,6 +200,22 @@ int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_
  * last call's contents (every part is rewritten before use): calls that overlap on the
  * GPU, on any stream or thread, race and corrupt each other. */
 int soax_sort_by_cell_noalloc(soax_t h, int32_t grid, uint32_t* perm_out, void* stream);
+
+/* ------------------------------------------------- Euler step (Eq. 1) */
+
+/* The paper's benchmark step x += dt*v (Eq. 1, Sec. 2) in single precision on the live
+ * f32 x 3 fields pos_field and vel_field (each update one rounded multiply and one
+ * rounded add).  per_component = 0: one fused pass over all six planes;
+ * per_component = 1: three launches, one per component, one element per thread (the
+ * paper's GPU SoA benchmark, Sec. 3.2). */
+int soax_euler(soax_t h, int32_t pos_field, int32_t vel_field, float dt, int32_t per_component,
+               void* stream);
+
+/* The same step on n AoS records of record_bytes bytes with f32 x[3] at byte x_off and
+ * f32 v[3] at byte v_off, one thread per record (Particle<SIZE> of Listing 4).  The
+ * buffer, the record size and the offsets must be multiples of 4 bytes. */
+int soax_euler_aos(void* rec, int64_t n, int64_t record_bytes, int64_t x_off, int64_t v_off, float dt,
+                   void* stream);
 
 /* ---------------------------------------------------------------- adjoint */
 

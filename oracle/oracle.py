@@ -15,6 +15,7 @@ in soax_oracle.c.  Functions:
   soa_to_aos / aos_to_soa                   byte-exact transposes (Listing 6)
   adjoint(...)                              loss and reverse-mode gradients
   euler_f32(x, v, dt)                       the paper's Eq. 1 step
+  euler_aos_f32(rec, rb, x_off, v_off, dt)  the same on Particle<SIZE> records (Listing 4)
 """
 import ctypes as C
 import os
@@ -51,6 +52,7 @@ def lib():
                                   [C.c_int, C.c_int] + [p] * 6 + [p, p, C.c_int])
         L.orc_adjoint.restype = C.c_int
         L.orc_euler_f32.argtypes = [i64, p, p, C.c_float]
+        L.orc_euler_aos_f32.argtypes = [i64, p, i64, i64, i64, C.c_float]
         _lib = L
     return _lib
 
@@ -210,3 +212,8 @@ def euler_f32(x, v, dt):
     _need(x, np.float32)
     _need(v, np.float32)
     lib().orc_euler_f32(x.size, _p(x), _p(v), np.float32(dt))
+
+
+def euler_aos_f32(rec, record_bytes, x_off, v_off, dt):
+    _need(rec, np.uint8)
+    lib().orc_euler_aos_f32(rec.size // record_bytes, _p(rec), record_bytes, x_off, v_off, np.float32(dt))

@@ -461,3 +461,15 @@ int orc_adjoint(int64_t n, const double* x0, const double* y0, const double* z0,
 void orc_euler_f32(int64_t n, float* x, const float* v, float dt) {
   for (int64_t i = 0; i < n; ++i) x[i] = x[i] + dt * v[i];
 }
+
+/* The same step on AoS records of rb bytes with f32 x[3] at x_off and f32 v[3] at
+ * v_off (the Particle<SIZE> record of Listing 4: x, v, then SIZE padding floats). */
+void orc_euler_aos_f32(int64_t n, uint8_t* rec, int64_t rb, int64_t x_off, int64_t v_off, float dt) {
+  for (int64_t i = 0; i < n; ++i) {
+    float x[3], v[3];
+    memcpy(x, rec + i * rb + x_off, sizeof x);
+    memcpy(v, rec + i * rb + v_off, sizeof v);
+    for (int c = 0; c < 3; ++c) x[c] = x[c] + dt * v[c];
+    memcpy(rec + i * rb + x_off, x, sizeof x);
+  }
+}

@@ -28,7 +28,7 @@ import torch
 from . import _abi
 from ._abi import DTYPES, STATUS_NAMES, soax_field_desc, soax_flow, soax_tune
 
-__all__ = ["SoaxError", "lib", "Particles", "Flow", "Tune", "radix_sort_pairs", "step_batched",
+__all__ = ["SoaxError", "lib", "Particles", "Flow", "Tune", "radix_sort_pairs", "step_batched", "euler_aos",
            "batched_workspace", "autotune", "sync", "SoaxRK2", "TWO_PI", "BASIC_SCHEMA", "WIDE_SCHEMA"]
 
 TWO_PI = 6.283185307179586
@@ -239,6 +239,12 @@ class Particles:
     def permute(self, perm, stream=None):
         _check(lib().soax_permute(self.h, _ptr(perm), _stream(stream)), "soax_permute")
 
+    def euler(self, dt, pos="x", vel="v", per_component=False, stream=None):
+        """The paper's Eq. 1 step x += dt*v on f32 x 3 fields (fused, or one launch per
+        component as the paper's GPU benchmark)."""
+        _check(lib().soax_euler(self.h, self.fidx(pos), self.fidx(vel), float(dt), int(bool(per_component)),
+                                _stream(stream)), "soax_euler")
+
     # ------------------------------------------------------------------ adjoint
     def adjoint_workspace(self, K, ckpt_every):
         b = C.c_size_t()
@@ -284,6 +290,12 @@ def radix_sort_pairs(keys, vals=None, key_bits=32, want_keys=True, ws=None, stre
     _check(lib().soax_radix_sort_pairs(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), n, int(key_bits), _ptr(ws),
                                        ws.numel(), _stream(stream)), "soax_radix_sort_pairs")
     return ko, vo
+
+
+def euler_aos(rec, n, record_bytes, x_off, v_off, dt, stream=None):
+    """Eq. 1 on n AoS records (f32 x[3] at x_off, f32 v[3] at v_off), in place."""
+    _check(lib().soax_euler_aos(_ptr(rec), int(n), int(record_bytes), int(x_off), int(v_off), float(dt),
+                                _stream(stream)), "soax_euler_aos")
 
 
 def _handles(parts):

@@ -51,6 +51,8 @@ SIGNATURES = {
     "soax_sort_by_cell": [_p, _i32, _p, _sz, _p],
     "soax_sort_results": [_p, _i32, _p, _sz, _P(_p), _P(_p)],
     "soax_sort_by_cell_noalloc": [_p, _i32, _p, _p],
+    "soax_euler": [_p, _i32, _i32, C.c_float, _i32, _p],
+    "soax_euler_aos": [_p, _i64, _i64, _i64, _i64, C.c_float, _p],
     "soax_adjoint_workspace_bytes": [_p, _i32, _i32, _P(_sz)],
     "soax_step_checkpointed": [_p, _P(soax_flow), _i32, _i32, _p, _sz, _p],
     "soax_step_adjoint": [_p, _P(soax_flow), _i32, _i32, _p, _sz, _P(_p), _P(_p), _P(_p), _P(_p), _p, _p],

@@ -3,13 +3,13 @@
 //
 // Each block stages kXRecs whole records in shared memory: the record side is moved
 // with 16-byte vector accesses over one contiguous byte range, the plane side with one
-// coalesced access per plane element.  Bytes are copied exactly; SoA -> AoS zeroes the
-// padding of every record.
+// coalesced access per plane element (thread t handles records t, t + 256, ...).  Bytes
+// are copied exactly; SoA -> AoS zeroes the padding of every record.
 #include "soax_internal.h"
 
 namespace soax {
 
-constexpr int kXRecs = 128;  // records per block (kXRecs * R is a multiple of 16 for any R)
+constexpr int kXRecs = 512;  // records per block (kXRecs * R is a multiple of 16 for any R)
 constexpr int kXThreads = 256;
 
 struct XArgs {
@@ -112,7 +112,7 @@ extern "C" int soax_aos_to_soa(soax_t h, const void* aos_dev, void* stream) {
   XArgs a;
   if (int r = make_xargs(h, const_cast<void*>(aos_dev), &a, "soax_aos_to_soa")) return r;
   const size_t sm = tile_smem(a.R);
-  if (sm > 200 * 1024) return fail(SOAX_EUNSUPPORTED, "soax_aos_to_soa: record too large");
+  if (sm > 200 * 1024) return fail(SOAX_EUNSUPPORTED, "soax_aos_to_soa: record larger than 400 bytes");
   if (int r = set_smem_attr((const void*)k_aos_to_soa, sm)) return r;
   k_aos_to_soa<<<grid_for(h->n, kXRecs), kXThreads, sm, as_stream(stream)>>>(a);
   return check_launch("soax_aos_to_soa");
@@ -124,7 +124,7 @@ extern "C" int soax_soa_to_aos(soax_t h, void* aos_dev, void* stream) {
   XArgs a;
   if (int r = make_xargs(h, aos_dev, &a, "soax_soa_to_aos")) return r;
   const size_t sm = tile_smem(a.R);
-  if (sm > 200 * 1024) return fail(SOAX_EUNSUPPORTED, "soax_soa_to_aos: record too large");
+  if (sm > 200 * 1024) return fail(SOAX_EUNSUPPORTED, "soax_soa_to_aos: record larger than 400 bytes");
   if (int r = set_smem_attr((const void*)k_soa_to_aos, sm)) return r;
   k_soa_to_aos<<<grid_for(h->n, kXRecs), kXThreads, sm, as_stream(stream)>>>(a);
   return check_launch("soax_soa_to_aos");

@@ -207,3 +207,26 @@ def test_euler_eq1_f32():
     ref = x + np.float32(1e-2) * v
     oracle.euler_f32(x, v, 1e-2)
     assert np.array_equal(x, ref)
+
+
+def test_euler_aos_equals_soa_listing4_records():
+    # Particle<SIZE> of Listing 4: float x[3]; float v[3]; float temp[SIZE].
+    rng = np.random.default_rng(12)
+    n, dt = 999, np.float32(1e-2)
+    x = [rng.standard_normal(n).astype(np.float32) for _ in range(3)]
+    v = [rng.standard_normal(n).astype(np.float32) for _ in range(3)]
+    for size in (0, 1, 32):
+        planes = x + v + [rng.standard_normal(n).astype(np.float32) for _ in range(size)]
+        ncomp = [3, 3] + ([size] if size else [])
+        eb = [4] * len(ncomp)
+        rec = oracle.soa_to_aos(planes, eb, ncomp)
+        rb, offs = oracle.aos_layout(eb, ncomp)
+        assert rb == 24 + 4 * size
+        oracle.euler_aos_f32(rec, rb, offs[0], offs[1], dt)
+        xs = [a.copy() for a in x]
+        for c in range(3):
+            oracle.euler_f32(xs[c], v[c], dt)
+        back = oracle.aos_to_soa(rec, eb, ncomp, [np.float32] * len(ncomp))
+        for c in range(3):
+            assert back[c].tobytes() == xs[c].tobytes()
+            assert np.array_equal(xs[c], x[c] + dt * v[c])
