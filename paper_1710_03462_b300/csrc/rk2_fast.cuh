@@ -152,17 +152,15 @@ __device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) {
   const uint64_t T = __umul64hi(X, SOAX_FOUR_OVER_PI_2P63) << 1;
   const uint64_t U = T + (1ull << 53);
   k = (int)(U >> 54) & (SOAX_TRIG_TABLE_SIZE - 1);
-  // rho = U mod 2^54 = residual + 2^53 in 2^-64 turns, 0 <= rho < 2^54.  Split into
-  // 23-bit pieces and convert each exactly by planting it in a float mantissa.
-  const uint32_t rl = (uint32_t)U, rh = (uint32_t)(U >> 32) & 0x3FFFFFu;
-  const uint32_t c0 = rl & 0x7FFFFFu;
-  const uint32_t c1 = __funnelshift_r(rl, rh, 23) & 0x7FFFFFu;
-  const uint32_t c2 = rh >> 14;
-  const float f0 = __fsub_rn(__uint_as_float(0x4B000000u | c0), 0x1p23f);        // c0
-  const float f1 = __fsub_rn(__uint_as_float(0x56800000u | c1), 0x1p46f);        // c1 2^23
-  const float f2 = __fsub_rn(__uint_as_float(0x62000000u | c2), 0x1.0001p69f);   // c2 2^46 - 2^53
-  const ff q = fast_two_sum(f2, f1);  // |f2| >= 2^46 > f1, or f2 == 0
-  const ff rt = {q.h, __fadd_rn(q.l, f0)};
+  // rho = U mod 2^54 = residual + 2^53 in 2^-64 turns, 0 <= rho < 2^54.  Its bits 31..53
+  // and 8..30 are converted exactly by planting each in a float mantissa; the 8 bits
+  // below are dropped (less than 2^-56 turn = 9e-17 rad).
+  const uint32_t rl = (uint32_t)U, rh = (uint32_t)(U >> 32);
+  const uint32_t chi = __funnelshift_r(rl, rh, 31) & 0x7FFFFFu;
+  const uint32_t clo = (rl >> 8) & 0x7FFFFFu;
+  const float fhi = __fsub_rn(__uint_as_float(0x5A800000u | chi), 0x1.8p54f);  // chi 2^31 - 2^53
+  const float flo = __fsub_rn(__uint_as_float(0x4F000000u | clo), 0x1p31f);    // clo 2^8
+  const ff rt = {fhi, flo};
   r = ff_mul(rt, ff{SOAX_TWO_PI_2M64_HI, SOAX_TWO_PI_2M64_LO});
 }
 
