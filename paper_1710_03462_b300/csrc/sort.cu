@@ -130,14 +130,19 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_upsweep(const uint32_t* __
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kTile;
   const uint32_t lt = (1u << lane) - 1;
-#pragma unroll 4
+  // All loads first, so that their latencies overlap.
+  uint32_t dg[kSortItems];
+#pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
-    int64_t i = base + (int64_t)j * kSortBlock + tid;
-    bool valid = i < n;
-    uint32_t d = valid ? ((keys[i] >> shift) & mask) : 0xFFFFFFFFu;
+    const int64_t i = base + (int64_t)j * kSortBlock + tid;
+    dg[j] = i < n ? ((keys[i] >> shift) & mask) : 0xFFFFFFFFu;
+  }
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
     // Warp-aggregated increment: sorted input puts many equal digits in one warp.
-    uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-    if (valid && (peers & lt) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    const uint32_t d = dg[j];
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (d != 0xFFFFFFFFu && (peers & lt) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
   for (int d = tid; d < radix; d += kSortBlock) {
@@ -190,23 +195,28 @@ __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
   const int tcount = (int)(n - tile0 < kTile ? n - tile0 : kTile);
   const uint32_t lt = (1u << lane) - 1;
   uint32_t kr[kSortItems], vr[kSortItems], rk[kSortItems];
+  // Load the warp's 512 elements first (their latencies overlap; the ranking loop below
+  // synchronises the warp, which would otherwise keep each load behind the previous
+  // round).
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int li = w * (kTile / kSortWarps) + r * 32 + lane;
+    const int64_t i = tile0 + li;
+    kr[r] = li < tcount ? keys_in[i] : 0u;
+    vr[r] = li < tcount ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
+  }
   // Stable ranking: warp w owns tile elements [w*512, (w+1)*512) in rounds of 32.
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int li = w * (kTile / kSortWarps) + r * 32 + lane;
     const bool valid = li < tcount;
-    const int64_t i = tile0 + li;
-    uint32_t key = valid ? keys_in[i] : 0u;
-    uint32_t val = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
-    uint32_t d = valid ? ((key >> shift) & mask) : 0xFFFFFFFFu;
-    uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    const uint32_t d = valid ? ((kr[r] >> shift) & mask) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
     uint32_t rank = 0;
     if (valid) rank = wc[w * radix + d] + __popc(peers & lt);
     __syncwarp();
     if (valid && (peers & lt) == 0) wc[w * radix + d] += __popc(peers);
     __syncwarp();
-    kr[r] = key;
-    vr[r] = val;
     rk[r] = rank;
   }
   __syncthreads();

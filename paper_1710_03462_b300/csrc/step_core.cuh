@@ -28,6 +28,11 @@ struct EnsArgs {
   float2 Af, Bf, Cf, itf, tsf;  // A, B, C, inv_tau, tau_scale as float pairs (hi, lo)
 };
 
+// 1/tau of particle i of ensemble e.
+__device__ __forceinline__ ff particle_inv_tau(const EnsArgs& e, int64_t i) {
+  return e.tau_src ? ff_inv_tau(e.tsf, e.tau_src[i]) : ff_from2(e.itf);
+}
+
 // The step constants of particle i of ensemble e (dt from f).
 __device__ __forceinline__ StepC make_stepc(const EnsArgs& e, const FlowK& f, int64_t i) {
   StepC c;
@@ -37,7 +42,7 @@ __device__ __forceinline__ StepC make_stepc(const EnsArgs& e, const FlowK& f, in
   c.dt = ff_from2(f.dtf);
   c.hdt = ff_from2(f.hdtf);
   c.dt_d = f.dt;
-  c.s = e.tau_src ? ff_inv_tau(e.tsf, e.tau_src[i]) : ff_from2(e.itf);
+  c.s = particle_inv_tau(e, i);
   return c;
 }
 
@@ -115,10 +120,16 @@ __device__ __forceinline__ void step_group(const EnsArgs& e, const FlowK& f, con
   load_f32<PPT, VB>(e.vy, i0, vy);
   load_f32<PPT, VB>(e.vz, i0, vz);
   float ax[PPT], ay[PPT], az[PPT];
+  ff sj[PPT];
 #pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    const StepC k = make_stepc(e, f, i0 + j);
-    for (int s = 0; s < nsteps; ++s) {
+  for (int j = 0; j < PPT; ++j) sj[j] = particle_inv_tau(e, i0 + j);
+  StepC k = make_stepc(e, f, i0);
+  // Steps outside, particles inside: the PPT particles' steps are independent, so the
+  // compiler can interleave them whatever the number of steps.
+  for (int s = 0; s < nsteps; ++s) {
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      k.s = sj[j];
       double p[3] = {x[j], y[j], z[j]};
       float v[3] = {vx[j], vy[j], vz[j]}, a[3];
       rk2_step(k, tab, p, v, a);
