@@ -11,6 +11,7 @@
 // scan); (3) every block ranks its tile stably (warp match + per-warp counters, in tile
 // order), stages the tile in shared memory in digit order and writes each digit's run
 // contiguously.  No block waits on another block, so nothing can hang.
+#include <cmath>
 #include <cstring>
 
 #include "soax_internal.h"
@@ -108,14 +109,31 @@ __device__ __forceinline__ int floor_mul_rn(double x, uint64_t cm, int ce) {
   return (int)(mr >> t);
 }
 
+// Cell index of one coordinate.  Fast path: P = x c 2^51 in fixed point (X = x 2^61
+// exact for 2^-8 <= x < 8, times c 2^54 rounded, high 64 bits) is within 3 units of the
+// exact product; the binary64 rounding of x c moves it by at most 2^-44 (x c < 2^10),
+// i.e. 128 units, so unless P lies within 131 units of an integer boundary its floor
+// equals floor(RN(x c)).  Otherwise (probability ~2^-42, or x < 2^-8) the exact path.
+__device__ __forceinline__ int cell_index(double x, uint64_t cfx, uint64_t cm, int ce) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)(b >> 52);  // sign bit included: negative x takes the exact path
+  if (e >= 1015 && e <= 1025) {
+    const uint64_t X = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (e - 1014);
+    const uint64_t P = __umul64hi(X, cfx);
+    const uint64_t frac = P & ((1ull << 51) - 1);
+    if (frac >= 131 && frac <= (1ull << 51) - 132) return (int)(P >> 51);
+  }
+  return floor_mul_rn(x, cm, ce);
+}
+
 __global__ void __launch_bounds__(256) k_cell_keys(const double* __restrict__ px, const double* __restrict__ py,
-                                                   const double* __restrict__ pz, int64_t n, uint64_t cm, int ce,
-                                                   int G, uint32_t* __restrict__ keys) {
+                                                   const double* __restrict__ pz, int64_t n, uint64_t cfx,
+                                                   uint64_t cm, int ce, int G, uint32_t* __restrict__ keys) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int ix = min(floor_mul_rn(px[i], cm, ce), G - 1);
-  int iy = min(floor_mul_rn(py[i], cm, ce), G - 1);
-  int iz = min(floor_mul_rn(pz[i], cm, ce), G - 1);
+  int ix = min(cell_index(px[i], cfx, cm, ce), G - 1);
+  int iy = min(cell_index(py[i], cfx, cm, ce), G - 1);
+  int iz = min(cell_index(pz[i], cfx, cm, ce), G - 1);
   keys[i] = (uint32_t)((iz * G + iy) * G + ix);
 }
 
@@ -364,7 +382,9 @@ extern "C" int soax_cell_keys(soax_t h, int32_t pos_field, int32_t grid, uint32_
   std::memcpy(&cb, &c, sizeof cb);
   const uint64_t cm = (cb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const int ce = (int)((cb >> 52) & 0x7FF);
-  k_cell_keys<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n, cm, ce, grid, keys);
+  // c 2^54 rounded to an integer (c < 2^8 for G <= 1024, so it fits 62 bits).
+  const uint64_t cfx = (uint64_t)std::llround(std::ldexp(c, 54));
+  k_cell_keys<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n, cfx, cm, ce, grid, keys);
   return check_launch("soax_cell_keys");
 }
 
