@@ -123,7 +123,7 @@ static int prepare(const soax_t* hs, const soax_flow* fls, int nens, const soax_
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (out->smem > 32 * 1024) {  // plus 16 KB of static shared memory (the sin/cos table)
+  if (out->smem > 16 * 1024) {  // plus 32 KB of static shared memory (the sin/cos table)
     cudaError_t e =
         cudaFuncSetAttribute((const void*)out->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
     if (e != cudaSuccess) return cuda_fail(e, "soax_step_batched: smem attribute");

@@ -2,10 +2,10 @@
 
     python paper_1710_03462_b300/csrc/gen_trig_table.py
 
-Entries, for k = 0..1023 and theta_k = 2 pi k / 1024 evaluated with 60-digit mpmath:
+Entries, for k = 0..2047 and theta_k = 2 pi k / 2048 evaluated with 60-digit mpmath:
 {hi(sin), lo(sin), hi(cos), lo(cos)} where hi = nearest float, lo = nearest float to the
 remainder, so hi + lo carries about 48 bits.  Constants: round(2^63 * 4/pi) for the
-fixed-point reduction of x to turns, 2 pi / 2^64 and 1/6 as float pairs.  Floats are
+fixed-point reduction of x to turns, and 2 pi / 2^64 as a float pair.  Floats are
 written as C hexadecimal literals, so the compiler reads them exactly.
 """
 import os
@@ -15,7 +15,7 @@ import numpy as np
 
 mpmath.mp.dps = 60
 HERE = os.path.dirname(os.path.abspath(__file__))
-M = 1024
+M = 2048
 
 
 def split(v):
@@ -38,16 +38,13 @@ def main():
         lines.append(f"  {{{hexf(sh)}, {hexf(sl)}, {hexf(ch)}, {hexf(cl)}}},")
     r63 = int(mpmath.nint(mpmath.mpf(2) ** 63 * 4 / mpmath.pi))
     kh, kl = split(2 * mpmath.pi / mpmath.mpf(2) ** 64)
-    s6h, s6l = split(mpmath.mpf(1) / 6)
     out = [
         "// Generated by gen_trig_table.py -- do not edit.",
-        "// {sin hi, sin lo, cos hi, cos lo} of 2 pi k / 1024, k = 0..1023.",
+        f"// {{sin hi, sin lo, cos hi, cos lo}} of 2 pi k / {M}, k = 0..{M - 1}.",
         f"#define SOAX_TRIG_TABLE_SIZE {M}",
         f"#define SOAX_FOUR_OVER_PI_2P63 0x{r63:016X}ull  // round(2^63 * 4/pi)",
         f"#define SOAX_TWO_PI_2M64_HI {hexf(kh)}  // 2 pi / 2^64 = hi + lo",
         f"#define SOAX_TWO_PI_2M64_LO {hexf(kl)}",
-        f"#define SOAX_SIXTH_HI {hexf(s6h)}  // 1/6 = hi + lo",
-        f"#define SOAX_SIXTH_LO {hexf(s6l)}",
         "#define SOAX_TRIG_TABLE_ENTRIES \\",
     ] + [ln + " \\" for ln in lines[:-1]] + [lines[-1].rstrip(",")]
     with open(os.path.join(HERE, "trig_table.inc"), "w") as fh:

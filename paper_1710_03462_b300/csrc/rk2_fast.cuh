@@ -20,8 +20,8 @@
 //    explicitly rounded intrinsics so the compiler cannot contract or reassociate them;
 //  * sin/cos of a position x in [0, 2pi) use an exact fixed-point reduction: x (binary64)
 //    becomes a 64-bit integer X = x 2^61, T = X (4/pi) 2^-63 is frac(x / 2pi) in 2^-64
-//    turns, its top 10 bits select theta_k = 2 pi k / 1024 from a float-float table and
-//    the rest is the residual r = x - theta_k (|r| <= pi/1024) as a float pair; then
+//    turns, its top 11 bits select theta_k = 2 pi k / 2048 from a float-float table and
+//    the rest is the residual r = x - theta_k (|r| <= pi/2048) as a float pair; then
 //    sin(theta_k + r) = S + (C sin r + S (cos r - 1)) with short Taylor series for the
 //    residual (a table-driven method in the manner of Tang);
 //  * sin/cos of the midpoint xm = x + (dt/2) v come from those of x by the angle
@@ -137,7 +137,7 @@ __device__ __forceinline__ ff ff_inv_tau(const float2 ts, float m) {
   return fast_two_sum(y0, __fmul_rn(y0, e));
 }
 
-// x (binary64, 0 <= x < 8) -> table index k and residual r = x - 2 pi k / 1024.
+// x (binary64, 0 <= x < 8) -> table index k and residual r = x - 2 pi k / 2048.
 __device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
   const int e = (int)((hi >> 20) & 0x7FFu);
@@ -150,39 +150,32 @@ __device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) {
     X = sh > -64 ? (m >> -sh) : 0ull;  // bits below 2^-61 dropped (< 5e-19)
   // T = X (4/pi) 2^-63 = frac(x / 2pi) 2^64 (within 3 units of the last place).
   const uint64_t T = __umul64hi(X, SOAX_FOUR_OVER_PI_2P63) << 1;
-  const uint64_t U = T + (1ull << 53);
-  k = (int)(U >> 54) & (SOAX_TRIG_TABLE_SIZE - 1);
-  // rho = U mod 2^54 = residual + 2^53 in 2^-64 turns, 0 <= rho < 2^54.  Its bits 31..53
-  // and 8..30 are converted exactly by planting each in a float mantissa; the 8 bits
-  // below are dropped (less than 2^-56 turn = 9e-17 rad).
+  const uint64_t U = T + (1ull << 52);
+  k = (int)(U >> 53) & (SOAX_TRIG_TABLE_SIZE - 1);
+  // rho = U mod 2^53 = residual + 2^52 in 2^-64 turns, 0 <= rho < 2^53.  Its bits 30..52
+  // and 7..29 are converted exactly by planting each in a float mantissa; the 7 bits
+  // below are dropped (less than 2^-57 turn = 5e-17 rad).
   const uint32_t rl = (uint32_t)U, rh = (uint32_t)(U >> 32);
-  const uint32_t chi = __funnelshift_r(rl, rh, 31) & 0x7FFFFFu;
-  const uint32_t clo = (rl >> 8) & 0x7FFFFFu;
-  const float fhi = __fsub_rn(__uint_as_float(0x5A800000u | chi), 0x1.8p54f);  // chi 2^31 - 2^53
-  const float flo = __fsub_rn(__uint_as_float(0x4F000000u | clo), 0x1p31f);    // clo 2^8
+  const uint32_t chi = __funnelshift_r(rl, rh, 30) & 0x7FFFFFu;
+  const uint32_t clo = (rl >> 7) & 0x7FFFFFu;
+  const float fhi = __fsub_rn(__uint_as_float(0x5A000000u | chi), 0x1.8p53f);  // chi 2^30 - 2^52
+  const float flo = __fsub_rn(__uint_as_float(0x4E800000u | clo), 0x1p30f);    // clo 2^7
   const ff rt = {fhi, flo};
   r = ff_mul(rt, ff{SOAX_TWO_PI_2M64_HI, SOAX_TWO_PI_2M64_LO});
 }
 
-// sin and cos of theta_k + r from the table entry (S, C) of theta_k and |r| <= 5e-3.
+// sin and cos of theta_k + r from the table entry (S, C) of theta_k and |r| <= pi/2048.
 __device__ __forceinline__ void sincos_tab(const float4 t, ff r, ff& s, ff& c) {
   ff p = two_prod(r.h, r.h);  // r^2
   p.l = __fmaf_rn(__fmul_rn(2.0f, r.h), r.l, p.l);
-  const float p2 = __fmul_rn(p.h, p.h);
-  // cos r - 1 = -r^2/2 + r^4/24 (r^6/720 < 2e-17 dropped)
-  const ff cm = {__fmul_rn(-0.5f, p.h), __fmaf_rn(p2, 1.0f / 24.0f, __fmul_rn(-0.5f, p.l))};
-  // sin r = r + r w, w = -r^2/6 + r^4/120
-  const float wh = __fmul_rn(p.h, -SOAX_SIXTH_HI);
-  float wl = __fmaf_rn(p.h, -SOAX_SIXTH_HI, -wh);
-  wl = __fmaf_rn(p.h, -SOAX_SIXTH_LO, wl);
-  wl = __fmaf_rn(p.l, -SOAX_SIXTH_HI, wl);
-  wl = __fmaf_rn(p2, 1.0f / 120.0f, wl);
-  const ff rw = ff_mul(r, ff{wh, wl});
-  ff sr = fast_two_sum(r.h, rw.h);
-  sr.l = __fadd_rn(sr.l, __fadd_rn(r.l, rw.l));
-  // Every table entry is 0 or at least sin(2pi/1024) = 6.1e-3 in magnitude while
-  // |r| <= pi/1024 = 3.1e-3, so in each sum below the first term is zero or the larger
-  // one: |S|, |C| > |C sr|, |S sr| >= 6.1e-3 |r| > r^2/2 >= |S cm|, |C cm|.
+  // cos r - 1 = -r^2/2 + r^4/24 (r^6/720 < 2e-20 dropped; r^4/24 < 3e-13 in float)
+  const ff cm = {__fmul_rn(-0.5f, p.h), __fmaf_rn(__fmul_rn(p.h, p.h), 1.0f / 24.0f, __fmul_rn(-0.5f, p.l))};
+  // sin r = r - r^3/6 (r^3/6 < 6e-10 is exact enough in float: error < 4e-17;
+  // r^5/120 < 8e-17 dropped)
+  const ff sr = {r.h, __fsub_rn(r.l, __fmul_rn(__fmul_rn(p.h, r.h), 1.0f / 6.0f))};
+  // Every table entry is 0 or at least sin(2pi/2048) = 3.07e-3 in magnitude while
+  // |r| <= pi/2048 = 1.54e-3, so in each sum below the first term is zero or the larger
+  // one: |S|, |C| > |C sr|, |S sr| >= 3.07e-3 |r| > r^2/2 >= |S cm|, |C cm|.
   const ff S = {t.x, t.y}, C = {t.z, t.w};
   const ff Ssr = ff_mul(S, sr), Csr = ff_mul(C, sr);
   s = ff_add_ordered(S, ff_add_ordered(Csr, ff_mul(S, cm)));
@@ -228,7 +221,7 @@ __device__ __forceinline__ void abc_u(const StepC& k, const ff s[3], const ff c[
 }
 
 // One step: x (binary64 position, in/out), v (f32 velocity, in/out), a2out (the last
-// stage acceleration rounded to f32).  tab: the 1024-entry table (shared memory).
+// stage acceleration rounded to f32).  tab: the 2048-entry table (shared memory).
 __device__ __forceinline__ void rk2_step_fast(const StepC& k, const float4* __restrict__ tab, double x[3],
                                               float v[3], float a2out[3]) {
   ff s0[3], c0[3], s1[3], c1[3], u0[3], u1[3];
@@ -318,7 +311,7 @@ __device__ __forceinline__ void rk2_reverse_fast(const StepC& k, const float4* _
 
 static __device__ const float4 kTrigTable[SOAX_TRIG_TABLE_SIZE] = {SOAX_TRIG_TABLE_ENTRIES};
 
-// Copy the table into shared memory (every thread of the block must call this).
+// Copy the table (32 KB) into shared memory (every thread of the block must call this).
 __device__ __forceinline__ void load_trig_table(float4* s_tab) {
   for (int i = threadIdx.x; i < SOAX_TRIG_TABLE_SIZE; i += blockDim.x) s_tab[i] = kTrigTable[i];
   __syncthreads();
