@@ -56,6 +56,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="soax", choices=["soax", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
+    ap.add_argument("--only", choices=["euler"], help="run only this secondary row (profiling)")
     ap.add_argument("--n", type=int, default=WL["n"], help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -450,8 +451,18 @@ def secondary_rows(sx, torch, p, d, dev):
     return rows
 
 
+def run_only(args):
+    import torch
+    import paper_1710_03462_b300 as sx
+    dev = torch.device("cuda", torch.cuda.current_device())
+    print(json.dumps({"only": args.only, "row": euler_replica(sx, torch, args.n, dev)}))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.only:
+        return run_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_soax(args)

@@ -113,9 +113,15 @@ int soax_destroy(soax_t h);
 /* Number of particles, fields, and planes of a handle (any output may be NULL). */
 int soax_size(soax_t h, int64_t* n, int32_t* nfields, int32_t* nplanes);
 
+/* resize (Listing 5) within the capacity given to soax_create: the particle count
+ * becomes n (0 <= n <= capacity, SOAX_EINVAL otherwise); elements n.. of the planes are
+ * left as they are (new elements hold whatever the buffers held). */
+int soax_set_size(soax_t h, int64_t n);
+
 /* Attach caller-owned device memory to plane (field, comp) of buffer set buf
  * (0 = primary, 1 = shadow used as the destination of soax_sort_by_cell).  dev_ptr
- * must hold n elements of the field's type and be 16-byte aligned (SOAX_EALIGN). */
+ * must hold capacity (the n given to soax_create) elements of the field's type and be
+ * 16-byte aligned (SOAX_EALIGN). */
 int soax_bind(soax_t h, int32_t field, int32_t comp, int32_t buf, void* dev_ptr);
 
 /* Which buffer set (0 or 1) currently holds the particles.  soax_sort_by_cell and
@@ -138,6 +144,26 @@ int soax_aos_to_soa(soax_t h, const void* aos_dev, void* stream);
 /* Bulk push_back (Listing 6): copy the live planes into n AoS records, byte for byte,
  * padding bytes written as 0. */
 int soax_soa_to_aos(soax_t h, void* aos_dev, void* stream);
+
+/* getElement / push_back for one particle (Listing 6): copy particle i (0 <= i < n) of
+ * the live planes into one AoS record at rec_dev (16-byte aligned device memory of
+ * soax_aos_layout's record size; padding written as 0), or the record into particle i.
+ * push_back = soax_set_size(h, n + 1) then soax_set_element(h, n, rec). */
+int soax_get_element(soax_t h, int64_t i, void* rec_dev, void* stream);
+int soax_set_element(soax_t h, int64_t i, const void* rec_dev, void* stream);
+
+/* Workspace bytes soax_remove needs for k removals. */
+int soax_remove_workspace_bytes(int64_t k, size_t* bytes);
+
+/* Remove the k particles at the distinct ascending indices idx (device u32, all < n) by
+ * overwriting them with the last particles (Sec. 2: a particle is removed by overwriting
+ * it with the last one when the order does not matter): the removed positions below
+ * n - k, ascending, receive the particles of positions n - k .. n - 1 that are not
+ * removed, ascending; nothing else moves.  The size becomes n - k at once for later
+ * calls.  If idx is not ascending, distinct and in
+ * range, nothing is moved and the kernel records SOAX_EINVAL for soax_sync (the size
+ * still drops by k). */
+int soax_remove(soax_t h, const uint32_t* idx, int64_t k, void* ws, size_t ws_bytes, void* stream);
 
 /* -------------------------------------------------------------------- step */
 
@@ -172,8 +198,10 @@ int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint
                           size_t ws_bytes, void* stream);
 
 /* out_f[i] = in_f[perm[i]] for every plane of every field, from the live buffer set to
- * the other one (apply-to-all-arrays, Listing 7), then flip the live set.  perm must be
- * a permutation of 0..n-1 (not checked). */
+ * the other one (apply-to-all-arrays, Listing 7), then flip the live set.  perm should be
+ * a permutation of 0..n-1; an entry >= n is not read (element 0 is gathered instead) and
+ * the kernel records SOAX_EINVAL in the device status word, which the next soax_sync
+ * returns. */
 int soax_permute(soax_t h, const uint32_t* perm, void* stream);
 
 /* Workspace bytes soax_sort_by_cell needs. */
@@ -200,6 +228,23 @@ int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_
  * last call's contents (every part is rewritten before use): calls that overlap on the
  * GPU, on any stream or thread, race and corrupt each other. */
 int soax_sort_by_cell_noalloc(soax_t h, int32_t grid, uint32_t* perm_out, void* stream);
+
+/* ------------------------------------------------- whole-array operations */
+
+/* SetToValue applied to every array (apply<F>(), Listing 7): every element of every
+ * plane of field (or of all fields when field == -1) of the live set becomes value,
+ * converted to the field's type as a C cast would.  SOAX_EINVAL (nothing written) if
+ * value is not exactly representable in an integer field, or overflows an f32 field. */
+int soax_fill(soax_t h, int32_t field, double value, void* stream);
+
+/* Fused elementwise expression over planes of the live set (the expression templates
+ * of Sec. 4.2, e.g. posArr(0) = velArr(1) - velArr(2) of Listing 5), one pass:
+ *   dst[i] = constant + sum_k coefs[k] * src_k[i],
+ * accumulated left to right with one fused multiply-add per term, in the planes' type
+ * (all planes f32, or all f64; coefficients rounded to it).  nterms in 0..8; src_fields,
+ * src_comps and coefs are host arrays of nterms entries; dst may be one of the sources. */
+int soax_lincomb(soax_t h, int32_t dst_field, int32_t dst_comp, int32_t nterms, const int32_t* src_fields,
+                 const int32_t* src_comps, const double* coefs, double constant, void* stream);
 
 /* ------------------------------------------------- Euler step (Eq. 1) */
 

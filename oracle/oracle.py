@@ -16,6 +16,9 @@ in soax_oracle.c.  Functions:
   adjoint(...)                              loss and reverse-mode gradients
   euler_f32(x, v, dt)                       the paper's Eq. 1 step
   euler_aos_f32(rec, rb, x_off, v_off, dt)  the same on Particle<SIZE> records (Listing 4)
+  fill(plane, value)                        SetToValue on one array (Listing 7)
+  lincomb(dst, srcs, coefs, constant)       dst = constant + sum coef_k src_k (Listing 5)
+  remove(planes, idx)                       removal by overwriting with the last ones (Sec. 2)
 """
 import ctypes as C
 import os
@@ -53,6 +56,10 @@ def lib():
         L.orc_adjoint.restype = C.c_int
         L.orc_euler_f32.argtypes = [i64, p, p, C.c_float]
         L.orc_euler_aos_f32.argtypes = [i64, p, i64, i64, i64, C.c_float]
+        L.orc_fill.argtypes = [i64, p, C.c_int, d]
+        L.orc_remove.argtypes = [i64, C.c_int, p, p, p, i64]
+        L.orc_remove.restype = i64
+        L.orc_lincomb.argtypes = [i64, C.c_int, p, C.c_int, p, p, d]
         _lib = L
     return _lib
 
@@ -217,3 +224,37 @@ def euler_f32(x, v, dt):
 def euler_aos_f32(rec, record_bytes, x_off, v_off, dt):
     _need(rec, np.uint8)
     lib().orc_euler_aos_f32(rec.size // record_bytes, _p(rec), record_bytes, x_off, v_off, np.float32(dt))
+
+
+_TCODES = {np.dtype(np.int32): 0, np.dtype(np.int64): 1, np.dtype(np.uint8): 2, np.dtype(np.float32): 3,
+           np.dtype(np.float64): 4}
+
+
+def fill(plane, value):
+    plane = np.ascontiguousarray(plane)
+    lib().orc_fill(plane.size, _p(plane), _TCODES[plane.dtype], float(value))
+    return plane
+
+
+def lincomb(dst, srcs, coefs, constant=0.0):
+    is32 = dst.dtype == np.float32
+    srcs = [_need(a, dst.dtype) for a in srcs]
+    _need(dst, dst.dtype)
+    arr = (C.c_void_p * max(1, len(srcs)))(*[a.ctypes.data for a in srcs])
+    cf = np.array(coefs, np.float64)
+    lib().orc_lincomb(dst.size, 1 if is32 else 0, _p(dst), len(srcs), arr, _p(cf), float(constant))
+    return dst
+
+
+def remove(planes, idx):
+    """Returns the planes after removing the particles at the ascending distinct indices
+    idx: removed positions below n - k receive the surviving particles of the last k
+    positions, both in ascending order."""
+    planes = [np.ascontiguousarray(a).copy() for a in planes]
+    idx = np.ascontiguousarray(idx, np.uint32)
+    n = planes[0].size
+    k = len(planes)
+    arr = (C.c_void_p * k)(*[a.ctypes.data for a in planes])
+    eb = np.array([a.dtype.itemsize for a in planes], np.int32)
+    m = lib().orc_remove(n, k, arr, _p(eb), _p(idx), idx.size)
+    return [a[:m].copy() for a in planes]

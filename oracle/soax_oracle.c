@@ -473,3 +473,64 @@ void orc_euler_aos_f32(int64_t n, uint8_t* rec, int64_t rb, int64_t x_off, int64
     memcpy(rec + i * rb + x_off, x, sizeof x);
   }
 }
+
+/* ------------------------------------------------ whole-array operations (Sec. 4) */
+/* SetToValue applied to one array (Listing 7): every element of a plane of elem_bytes
+ * bytes and type code tcode (0 i32, 1 i64, 2 u8, 3 f32, 4 f64) set to value. */
+void orc_fill(int64_t n, void* plane, int tcode, double value) {
+  for (int64_t i = 0; i < n; ++i) {
+    switch (tcode) {
+      case 0: ((int32_t*)plane)[i] = (int32_t)value; break;
+      case 1: ((int64_t*)plane)[i] = (int64_t)value; break;
+      case 2: ((uint8_t*)plane)[i] = (uint8_t)value; break;
+      case 3: ((float*)plane)[i] = (float)value; break;
+      default: ((double*)plane)[i] = value; break;
+    }
+  }
+}
+
+/* dst = constant + sum_k coef_k src_k, element by element, accumulated left to right with
+ * one fused multiply-add per term (acc = fma(coef_k, src_k, acc)), in the planes' type
+ * (all f32 when is_f32, else all f64; coefficients and constant rounded to it).  The
+ * expression of Listing 5, posArr(0) = velArr(1) - velArr(2), is constant 0 and
+ * coefficients (1, -1). */
+void orc_lincomb(int64_t n, int is_f32, void* dst, int nterms, const void* const* src, const double* coef,
+                 double constant) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (is_f32) {
+      float acc = (float)constant;
+      for (int k = 0; k < nterms; ++k) acc = fmaf((float)coef[k], ((const float*)src[k])[i], acc);
+      ((float*)dst)[i] = acc;
+    } else {
+      double acc = constant;
+      for (int k = 0; k < nterms; ++k) acc = fma(coef[k], ((const double*)src[k])[i], acc);
+      ((double*)dst)[i] = acc;
+    }
+  }
+}
+
+/* Removal by overwriting with the last particles (Sec. 2: a particle is removed by
+ * overwriting it with the last one, the default of SoAx when the order does not
+ * matter).  For k distinct ascending indices and m = n - k: the removed positions below
+ * m ("holes", ascending) receive the particles at the positions m..n-1 that are not
+ * removed (ascending), one each, in every plane; nothing else moves.  For k = 1 this is
+ * exactly "overwrite with the last".  Returns m. */
+int64_t orc_remove(int64_t n, int nplanes, void* const* planes, const int32_t* elem_bytes, const uint32_t* idx,
+                   int64_t k) {
+  int64_t m = n - k;
+  uint8_t* removed = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!removed) return -1;
+  for (int64_t j = 0; j < k; ++j) removed[idx[j]] = 1;
+  int64_t src = m;
+  for (int64_t j = 0; j < k && idx[j] < (uint32_t)m; ++j) {
+    while (removed[src]) ++src;  /* next surviving tail particle */
+    for (int f = 0; f < nplanes; ++f) {
+      uint8_t* p = (uint8_t*)planes[f];
+      int64_t e = elem_bytes[f];
+      memcpy(p + (int64_t)idx[j] * e, p + src * e, (size_t)e);
+    }
+    ++src;
+  }
+  free(removed);
+  return m;
+}

@@ -173,11 +173,12 @@ class Particles:
         for name, comps in arrays.items():
             dst = self.field(name)
             for c, a in enumerate(comps):
-                dst[c].copy_(torch.as_tensor(a))
+                a = torch.as_tensor(a)
+                dst[c][: a.shape[0]].copy_(a)
 
     def numpy(self):
-        """Live planes as numpy arrays (synchronises)."""
-        return {name: [t.cpu().numpy() for t in self.field(name)] for name in self._names}
+        """Live planes (the current size) as numpy arrays (synchronises)."""
+        return {name: [t[:self.n].cpu().numpy() for t in self.field(name)] for name in self._names}
 
     def flow(self, f: Flow):
         return soax_flow(f.A, f.B, f.C, f.tau, f.dt, f.tau_scale,
@@ -238,6 +239,59 @@ class Particles:
 
     def permute(self, perm, stream=None):
         _check(lib().soax_permute(self.h, _ptr(perm), _stream(stream)), "soax_permute")
+
+    @property
+    def size(self):
+        n = C.c_int64()
+        _check(lib().soax_size(self.h, C.byref(n), None, None))
+        return n.value
+
+    def set_size(self, n):
+        """resize within the capacity given at construction (Listing 5)."""
+        _check(lib().soax_set_size(self.h, int(n)), "soax_set_size")
+        self.n = int(n)
+
+    def get_element(self, i, stream=None):
+        """Particle i as one AoS record (uint8 tensor of the record size, Listing 6)."""
+        rb, _ = self.aos_layout()
+        rec = torch.empty(max(rb, 16), dtype=torch.uint8, device=self.device)
+        _check(lib().soax_get_element(self.h, int(i), _ptr(rec), _stream(stream)), "soax_get_element")
+        return rec[:rb]
+
+    def set_element(self, i, rec, stream=None):
+        _check(lib().soax_set_element(self.h, int(i), _ptr(rec), _stream(stream)), "soax_set_element")
+
+    def push_back(self, rec, stream=None):
+        """Append one particle given as an AoS record (needs spare capacity)."""
+        n = self.size
+        self.set_size(n + 1)
+        self.set_element(n, rec, stream)
+
+    def remove(self, idx, stream=None):
+        """Remove the particles at distinct ascending indices (int32 tensor) by overwriting
+        each with the last one (Sec. 2)."""
+        k = idx.numel()
+        b = C.c_size_t()
+        _check(lib().soax_remove_workspace_bytes(k, C.byref(b)))
+        ws = torch.empty(max(b.value, 16), dtype=torch.uint8, device=self.device)
+        _check(lib().soax_remove(self.h, _ptr(idx), k, _ptr(ws), ws.numel(), _stream(stream)), "soax_remove")
+        self.n -= k
+
+    def fill(self, value, field=None, stream=None):
+        """SetToValue on every array of a field, or of all fields (Listing 7)."""
+        _check(lib().soax_fill(self.h, -1 if field is None else self.fidx(field), float(value), _stream(stream)),
+               "soax_fill")
+
+    def lincomb(self, dst, terms, constant=0.0, stream=None):
+        """dst = constant + sum coef * src in one pass; dst and each src are (field, comp),
+        terms a list of ((field, comp), coef).  E.g. Listing 5's
+        posArr(0) = velArr(1) - velArr(2): lincomb(("pos", 0), [(("vel", 1), 1), (("vel", 2), -1)])."""
+        k = len(terms)
+        fs = (C.c_int32 * max(1, k))(*[self.fidx(t[0][0]) for t in terms])
+        cs = (C.c_int32 * max(1, k))(*[int(t[0][1]) for t in terms])
+        co = (C.c_double * max(1, k))(*[float(t[1]) for t in terms])
+        _check(lib().soax_lincomb(self.h, self.fidx(dst[0]), int(dst[1]), k, fs, cs, co, float(constant),
+                                  _stream(stream)), "soax_lincomb")
 
     def euler(self, dt, pos="x", vel="v", per_component=False, stream=None):
         """The paper's Eq. 1 step x += dt*v on f32 x 3 fields (fused, or one launch per

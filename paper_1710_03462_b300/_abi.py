@@ -35,12 +35,17 @@ SIGNATURES = {
     "soax_create": [_P(soax_field_desc), _i32, _i64, _P(_p)],
     "soax_destroy": [_p],
     "soax_size": [_p, _P(_i64), _P(_i32), _P(_i32)],
+    "soax_set_size": [_p, _i64],
     "soax_bind": [_p, _i32, _i32, _i32, _p],
     "soax_current": [_p, _P(_i32)],
     "soax_set_current": [_p, _i32],
     "soax_aos_layout": [_p, _P(_i64), _P(_i64)],
     "soax_aos_to_soa": [_p, _p, _p],
     "soax_soa_to_aos": [_p, _p, _p],
+    "soax_get_element": [_p, _i64, _p, _p],
+    "soax_set_element": [_p, _i64, _p, _p],
+    "soax_remove_workspace_bytes": [_i64, _P(_sz)],
+    "soax_remove": [_p, _p, _i64, _p, _sz, _p],
     "soax_step": [_p, _P(soax_flow), _i32, _p],
     "soax_step_aos": [_p, _p, _P(soax_flow), _i32, _p],
     "soax_cell_keys": [_p, _i32, _i32, _p, _p],
@@ -51,6 +56,8 @@ SIGNATURES = {
     "soax_sort_by_cell": [_p, _i32, _p, _sz, _p],
     "soax_sort_results": [_p, _i32, _p, _sz, _P(_p), _P(_p)],
     "soax_sort_by_cell_noalloc": [_p, _i32, _p, _p],
+    "soax_fill": [_p, _i32, C.c_double, _p],
+    "soax_lincomb": [_p, _i32, _i32, _i32, _p, _p, _p, C.c_double, _p],
     "soax_euler": [_p, _i32, _i32, C.c_float, _i32, _p],
     "soax_euler_aos": [_p, _i64, _i64, _i64, _i64, C.c_float, _p],
     "soax_adjoint_workspace_bytes": [_p, _i32, _i32, _P(_sz)],

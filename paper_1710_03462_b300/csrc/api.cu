@@ -1,5 +1,6 @@
 // Handle management, schema validation, AoS layout and status reporting.
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <set>
 
@@ -41,6 +42,20 @@ int dtype_size(int dtype) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+int* status_word() {
+  static std::mutex mu;
+  static int* ptr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    ptr[dev] = static_cast<int*>(p);
+  }
+  return ptr[dev];
+}
+
 int check_handle(soax_t h) {
   if (!h) return fail(SOAX_EINVAL, "null handle");
   return SOAX_OK;
@@ -79,6 +94,7 @@ extern "C" int soax_create(const soax_field_desc* fields, int32_t nfields, int64
   soax_s* h = new (std::nothrow) soax_s();
   if (!h) return fail(SOAX_EINVAL, "soax_create: out of host memory");
   h->n = n;
+  h->capacity = n;
   std::set<std::string> names;
   int plane = 0;
   for (int f = 0; f < nfields; ++f) {
@@ -126,6 +142,14 @@ extern "C" int soax_size(soax_t h, int64_t* n, int32_t* nfields, int32_t* nplane
   if (n) *n = h->n;
   if (nfields) *nfields = (int32_t)h->fields.size();
   if (nplanes) *nplanes = h->nplanes;
+  return SOAX_OK;
+}
+
+extern "C" int soax_set_size(soax_t h, int64_t n) {
+  if (int e = check_handle(h)) return e;
+  if (n < 0 || n > h->capacity)
+    return fail(SOAX_EINVAL, "soax_set_size: n must be in 0..capacity (" + std::to_string(h->capacity) + ")");
+  h->n = n;
   return SOAX_OK;
 }
 

@@ -27,7 +27,8 @@ struct Field {
 }  // namespace soax
 
 struct soax_s {
-  int64_t n = 0;
+  int64_t n = 0;         // current number of particles
+  int64_t capacity = 0;  // n at creation: every bound plane holds this many elements
   std::vector<soax::Field> fields;
   int nplanes = 0;
   void* planes[2][soax::kMaxPlanes] = {};
@@ -46,6 +47,8 @@ int cuda_fail(cudaError_t e, const char* what);
 int check_launch(const char* what);
 
 int dtype_size(int dtype);
+// Device address of this device's status word (looked up once per device), or null.
+int* status_word();
 bool aligned16(const void* p);
 
 // Validation helpers used by several entry points.

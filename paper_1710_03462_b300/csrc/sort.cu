@@ -288,13 +288,22 @@ struct PermArgs {
   int nplanes;
   int64_t n;
   const uint32_t* perm;
+  int* status;  // device status word: an index >= n is recorded here and not read
 };
 
 __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArgs a) {
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (i0 >= a.n) return;
   if (i0 + 4 <= a.n) {
-    const uint4 p = *reinterpret_cast<const uint4*>(a.perm + i0);
+    uint4 p = *reinterpret_cast<const uint4*>(a.perm + i0);
+    if (p.x >= a.n || p.y >= a.n || p.z >= a.n || p.w >= a.n) {
+      // Not a permutation of 0..n-1: report and gather element 0 instead.
+      atomicExch(a.status, (int)SOAX_EINVAL);
+      if (p.x >= a.n) p.x = 0;
+      if (p.y >= a.n) p.y = 0;
+      if (p.z >= a.n) p.z = 0;
+      if (p.w >= a.n) p.w = 0;
+    }
     for (int f = 0; f < a.nplanes; ++f) {
       const int es = a.es[f];
       if (es == 8) {
@@ -314,7 +323,11 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArg
     }
   } else {
     for (int64_t i = i0; i < a.n; ++i) {
-      const uint32_t p = a.perm[i];
+      uint32_t p = a.perm[i];
+      if (p >= a.n) {
+        atomicExch(a.status, (int)SOAX_EINVAL);
+        p = 0;
+      }
       for (int f = 0; f < a.nplanes; ++f) {
         const int es = a.es[f];
         if (es == 8)
@@ -471,6 +484,8 @@ extern "C" int soax_permute(soax_t h, const uint32_t* perm, void* stream) {
   a.nplanes = h->nplanes;
   a.n = h->n;
   a.perm = perm;
+  a.status = status_word();
+  if (!a.status) return fail(SOAX_ECUDA, "soax_permute: status word");
   k_permute<<<grid_for((h->n + 3) / 4, 256), 256, 0, as_stream(stream)>>>(a);
   if (int r = check_launch("soax_permute")) return r;
   h->current = dst;

@@ -75,19 +75,19 @@ __global__ void __launch_bounds__(kXThreads) k_soa_to_aos(const __grid_constant_
   for (int64_t k = (f16 << 4) + threadIdx.x; k < bytes; k += kXThreads) dst[k] = tile[k];
 }
 
-static int make_xargs(soax_t h, void* rec, XArgs* a, const char* who) {
+static int make_xargs(soax_t h, void* rec, XArgs* a, const char* who, int64_t first = 0, int64_t count = -1) {
   if (int r = live_planes_bound(h, h->current)) return r;
   if (!rec) return fail(SOAX_EINVAL, std::string(who) + ": records pointer is NULL");
   if (!aligned16(rec)) return fail(SOAX_EALIGN, std::string(who) + ": records not 16-byte aligned");
   int p = 0;
   for (size_t f = 0; f < h->fields.size(); ++f)
     for (int c = 0; c < h->fields[f].ncomp; ++c, ++p) {
-      a->planes[p] = h->planes[h->current][p];
+      a->planes[p] = static_cast<char*>(h->planes[h->current][p]) + first * h->fields[f].esize;
       a->es[p] = h->fields[f].esize;
       a->off[p] = (int32_t)(h->offsets[f] + (int64_t)c * h->fields[f].esize);
     }
   a->nplanes = h->nplanes;
-  a->n = h->n;
+  a->n = count < 0 ? h->n : count;
   a->R = h->record_bytes;
   a->rec = static_cast<char*>(rec);
   return SOAX_OK;
@@ -128,4 +128,22 @@ extern "C" int soax_soa_to_aos(soax_t h, void* aos_dev, void* stream) {
   if (int r = set_smem_attr((const void*)k_soa_to_aos, sm)) return r;
   k_soa_to_aos<<<grid_for(h->n, kXRecs), kXThreads, sm, as_stream(stream)>>>(a);
   return check_launch("soax_soa_to_aos");
+}
+
+extern "C" int soax_get_element(soax_t h, int64_t i, void* rec_dev, void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (i < 0 || i >= h->n) return fail(SOAX_EINVAL, "soax_get_element: index out of range");
+  XArgs a;
+  if (int r = make_xargs(h, rec_dev, &a, "soax_get_element", i, 1)) return r;
+  k_soa_to_aos<<<1, kXThreads, (size_t)((a.R + 15) / 16 * 16), as_stream(stream)>>>(a);
+  return check_launch("soax_get_element");
+}
+
+extern "C" int soax_set_element(soax_t h, int64_t i, const void* rec_dev, void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (i < 0 || i >= h->n) return fail(SOAX_EINVAL, "soax_set_element: index out of range");
+  XArgs a;
+  if (int r = make_xargs(h, const_cast<void*>(rec_dev), &a, "soax_set_element", i, 1)) return r;
+  k_aos_to_soa<<<1, kXThreads, (size_t)((a.R + 15) / 16 * 16), as_stream(stream)>>>(a);
+  return check_launch("soax_set_element");
 }

@@ -143,3 +143,22 @@ def test_cell_keys_near_every_boundary(G):
     p = sx.Particles([("pos", "f64", 3, "P")], x.size)
     p.load({"pos": pos})
     assert np.array_equal(_u32(p.cell_keys(G)), oracle.cell_keys(*pos, G))
+
+
+def test_permute_reports_an_index_out_of_range():
+    """A bad permutation entry is not read; the kernel records EINVAL in the device status
+    word and soax_sync reports it (and clears it)."""
+    n = 1000
+    d = soax_inputs.basic_set(n, 9)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    p.load(d)
+    perm = torch.arange(n, dtype=torch.int32, device="cuda")
+    perm[517] = n + 12345
+    p.permute(perm)
+    with pytest.raises(sx.SoaxError) as ei:
+        sx.sync()
+    assert ei.value.code == -1
+    sx.sync()  # cleared
+    g = p.numpy()
+    assert g["id"][0][517] == d["id"][0][0]
+    assert np.array_equal(np.delete(g["id"][0], 517), np.delete(d["id"][0], 517))

@@ -230,3 +230,41 @@ def test_euler_aos_equals_soa_listing4_records():
         for c in range(3):
             assert back[c].tobytes() == xs[c].tobytes()
             assert np.array_equal(xs[c], x[c] + dt * v[c])
+
+
+def test_fill_and_lincomb_pins():
+    # SetToValue (Listing 7) on each type; the expression of Listing 5 against numpy.
+    for dt, val in ((np.int32, -7), (np.int64, 2 ** 40), (np.uint8, 200), (np.float32, 0.1), (np.float64, 0.1)):
+        a = oracle.fill(np.zeros(17, dt), val)
+        assert np.all(a == np.array(val).astype(dt))
+    rng = np.random.default_rng(3)
+    for dt in (np.float32, np.float64):
+        v1, v2 = rng.standard_normal(1000).astype(dt), rng.standard_normal(1000).astype(dt)
+        out = oracle.lincomb(np.empty(1000, dt), [v1, v2], [1.0, -1.0])
+        assert np.array_equal(out, v1 - v2)  # fma(1, a, 0) = a exactly, then fma(-1, b, a) = RN(a - b)
+        w = oracle.lincomb(np.empty(1000, dt), [v1], [2.0], 0.5)
+        assert np.array_equal(w, (dt(2.0) * v1 + dt(0.5)).astype(dt))  # 2 v1 is exact: one rounding
+
+
+def test_remove_by_overwrite_with_last_pins():
+    # Brute force on the definition: the survivors are the same multiset, the size drops by
+    # k, and elements below the new size that were not removed stay in place.
+    rng = np.random.default_rng(4)
+    for n, k in ((10, 0), (10, 10), (10, 3), (1000, 37), (1000, 999)):
+        ids = np.arange(n, dtype=np.int64)
+        idx = np.sort(rng.choice(n, k, replace=False)).astype(np.uint32)
+        out = oracle.remove([ids], idx)[0]
+        assert out.size == n - k
+        assert sorted(out.tolist()) == sorted(set(range(n)) - set(idx.tolist()))
+        keep = [i for i in range(n - k) if i not in set(idx.tolist())]
+        assert np.array_equal(out[keep], ids[keep])
+    # Sec. 2: removing one particle overwrites it with the last one.
+    for i in range(7):
+        out = oracle.remove([np.arange(7, dtype=np.int32)], np.array([i], np.uint32))[0]
+        exp = list(range(6))
+        if i < 6:
+            exp[i] = 6
+        assert out.tolist() == exp
+    # Holes below n - k take the surviving tail particles in ascending order.
+    out = oracle.remove([np.arange(10, dtype=np.int32)], np.array([2, 4, 7], np.uint32))[0]
+    assert out.tolist() == [0, 1, 8, 3, 9, 5, 6]
