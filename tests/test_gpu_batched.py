@@ -82,3 +82,37 @@ def test_mixed_flows_per_ensemble():
         p.step(f, 4)
     assert _bytes(parts) == _bytes(solo)
     assert _bytes(parts)[:6] != _bytes(parts)[6:]
+
+
+def test_full_size_batched_512_sampled():
+    """The 512-ensemble workload (3.0e8 particles), 20 steps in one persistent launch per
+    step: every 64th ensemble checked on sampled particles against the oracle with its
+    own amplitudes and tau."""
+    import oracle
+    from parity import assert_parity
+    w = soax_inputs.WORKLOADS["batched_512"]
+    sizes, taus, abc = soax_inputs.ensembles(w["nens"], w["nmin"], w["nmax"], w["seed"])
+    parts, flows, data = [], [], {}
+    for e, (ne, tau) in enumerate(zip(sizes, taus)):
+        dset = soax_inputs.ensemble_set(e, ne)
+        p = sx.Particles(SCHEMA, int(ne), shadow=False)
+        p.load(dset)
+        parts.append(p)
+        flows.append(sx.Flow(A=abc[e, 0], B=abc[e, 1], C=abc[e, 2], tau=float(tau), dt=w["dt"]))
+        if e % 64 == 0:
+            data[e] = dset
+    steps = 20
+    sx.step_batched(parts, flows, steps)
+    for e, dset in data.items():
+        n = int(sizes[e])
+        idx = np.arange(0, n, max(1, n // 512))
+        g = parts[e].numpy()
+        x0 = [np.ascontiguousarray(a[idx]) for a in dset["pos"]]
+        v0 = [np.ascontiguousarray(a[idx]) for a in dset["vel"]]
+        opos, ovel = [a.copy() for a in x0], [a.copy() for a in v0]
+        f = flows[e]
+        oracle.step_soa(opos, ovel, f.A, f.B, f.C, f.tau, f.dt, steps)
+        assert_parity([a[idx] for a in g["pos"]], [a[idx] for a in g["vel"]], opos, ovel, x0, v0,
+                      np.full(idx.size, f.tau), f.A, f.B, f.C, f.dt, steps)
+    del parts
+    torch.cuda.empty_cache()

@@ -137,3 +137,12 @@ def test_full_size_wide_n64M_sampled():
                   w["dt"], steps)
     del p
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("A,B,C,tau,dt", [(1.5, 0.5, 1.3, 0.01, 1e-3), (0.7, 1.4, 0.9, 0.05, 1e-3),
+                                          (1.2, 1.1, 0.6, 0.2, 5e-4)])
+def test_step_amplitudes_and_stiff_tau(A, B, C, tau, dt):
+    """Non-unit amplitudes and dt/tau up to 0.1, the range of the batched workload."""
+    n, steps = 20001, 100
+    d, g, opos, ovel = _run_both(n, steps, A, B, C, tau, dt, seed=int(tau * 1000))
+    assert_parity(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], np.full(n, tau), A, B, C, dt, steps)
