@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_forward(EnsArgs e, FlowK f, i
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= e.n) return;
   const StepC k = make_stepc(e, f, i);
+  const TrigUnscaled tg = trig_unscaled(s_tab, e);
   double x[3] = {e.px[i], e.py[i], e.pz[i]};
   float v[3] = {e.vx[i], e.vy[i], e.vz[i]}, a[3] = {0.f, 0.f, 0.f};
   for (int s = 0; s < K; ++s) {
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_forward(EnsArgs e, FlowK f, i
         r.v[c][i] = v[c];
       }
     }
-    rk2_step(k, s_tab, x, v, a);
+    rk2_step<true>(k, tg, x, v, a);
   }
   e.px[i] = x[0]; e.py[i] = x[1]; e.pz[i] = x[2];
   e.vx[i] = v[0]; e.vy[i] = v[1]; e.vz[i] = v[2];
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, i
   double th[4] = {0.0, 0.0, 0.0, 0.0};
   if (i < e.n) {
     const StepC k = make_stepc(e, f, i);
+    const TrigUnscaled tg = trig_unscaled(s_tab, e);
     ff xb[3], vb[3], tf[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int c = 0; c < 3; ++c) {
       xb[c] = d2ff(io.xbK[c][i]);
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, i
           st.x[c][i] = x[c];
           st.v[c][i] = v[c];
         }
-        rk2_step(k, s_tab, x, v, a);
+        rk2_step<false>(k, tg, x, v, a);
       }
       for (int j = len - 1; j >= 0; --j) {
         StateRef st = state_at(stack, sb, e.n, j);

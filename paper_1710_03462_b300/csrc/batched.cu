@@ -42,10 +42,16 @@ __global__ void __launch_bounds__(512) k_step_batched(const EnsArgs* __restrict_
     const EnsArgs e = ens[lo];
     const int64_t i0 = (t - s_prefix[lo]) * tile_parts + (int64_t)threadIdx.x * PPT;
     if (i0 < e.n) {
-      if (i0 + PPT <= e.n)
-        step_group<PPT, VB>(e, f, s_tab, i0, nsteps_inner);
-      else
-        step_tail(e, f, s_tab, i0, (int)(e.n - i0), nsteps_inner);
+      const StepC kc = make_stepc(e, f);
+      const TrigUnscaled tg = trig_unscaled(s_tab, e);
+      const int64_t cnt = e.n - i0;
+      if (e.tau_src) {
+        if (e.ax) step_span_t<PPT, VB, true, true>(e, kc, tg, i0, cnt, nsteps_inner);
+        else step_span_t<PPT, VB, true, false>(e, kc, tg, i0, cnt, nsteps_inner);
+      } else {
+        if (e.ax) step_span_t<PPT, VB, false, true>(e, kc, tg, i0, cnt, nsteps_inner);
+        else step_span_t<PPT, VB, false, false>(e, kc, tg, i0, cnt, nsteps_inner);
+      }
     }
   }
 }

@@ -121,10 +121,12 @@ __device__ __forceinline__ double f2d_exact(float f) {
 
 // Per-particle constants of the step, as float pairs.
 struct StepC {
-  ff A, B, C;  // flow amplitudes
-  ff dt, hdt;  // dt and dt/2
-  ff s;        // 1/tau
-  double dt_d; // dt as binary64, for the position update
+  ff A, B, C;    // flow amplitudes (the reverse pass; the forward step reads them from its table)
+  ff dt, hdt;    // dt and dt/2
+  ff s;          // 1/tau
+  ff hs, ds, gh; // (dt/2)/tau, dt/tau and 1 - (dt/2)/tau (set_inv_tau)
+  double dt_d;   // dt as binary64, for the position update
+  float vnear;   // SOAX_SHIFT_MAX / (dt/2): the speeds the shift series covers
 };
 
 __device__ __forceinline__ ff ff_from2(const float2 p) { return ff{p.x, p.y}; }
@@ -135,6 +137,14 @@ __device__ __forceinline__ ff ff_inv_tau(const float2 ts, float m) {
   const float y0 = __frcp_rn(t.h);
   const float e = __fsub_rn(__fmaf_rn(-t.h, y0, 1.0f), __fmul_rn(t.l, y0));
   return fast_two_sum(y0, __fmul_rn(y0, e));
+}
+
+// s = 1/tau and the products of the update that depend on it alone.
+__device__ __forceinline__ void set_inv_tau(StepC& k, ff s) {
+  k.s = s;
+  k.hs = ff_mul(k.hdt, s);
+  k.ds = ff_mul(k.dt, s);
+  k.gh = ff_add_f(ff{-k.hs.h, -k.hs.l}, 1.0f);
 }
 
 // x (binary64, 0 <= x < 8) -> table index k and residual r = x - 2 pi k / 2048.
@@ -164,7 +174,28 @@ __device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) {
   r = ff_mul(rt, ff{SOAX_TWO_PI_2M64_HI, SOAX_TWO_PI_2M64_LO});
 }
 
-// sin and cos of theta_k + r from the table entry (S, C) of theta_k and |r| <= pi/2048.
+// amp times the table entry t = (sin, cos) as float pairs, packed like the entry.
+__device__ __forceinline__ float4 scale_entry(ff amp, float4 t) {
+  const ff a = ff_mul(amp, ff{t.x, t.y}), b = ff_mul(amp, ff{t.z, t.w});
+  return make_float4(a.h, a.l, b.h, b.l);
+}
+
+// Each coordinate enters u with one amplitude, for its sine and its cosine alike:
+// x with B, y with C, z with A.  The forward step therefore reads amplitude-scaled
+// entries P = a sin, Q = a cos, from one of two sources that give identical bits:
+// three tables scaled once per block, or the plain table scaled per lookup.
+struct TrigScaled {
+  const float4* __restrict__ t;  // 3 x SOAX_TRIG_TABLE_SIZE entries: x, y, z
+  __device__ __forceinline__ float4 operator()(int c, int k) const { return t[c * SOAX_TRIG_TABLE_SIZE + k]; }
+};
+struct TrigUnscaled {
+  const float4* __restrict__ t;  // the plain table
+  ff amp[3];                     // B, C, A
+  __device__ __forceinline__ float4 operator()(int c, int k) const { return scale_entry(amp[c], t[k]); }
+};
+
+// a sin and a cos of theta_k + r from the entry (S, C) = (a sin theta_k, a cos theta_k)
+// of a table scaled by the amplitude a (a = 1: the plain table), |r| <= pi/2048.
 __device__ __forceinline__ void sincos_tab(const float4 t, ff r, ff& s, ff& c) {
   ff p = two_prod(r.h, r.h);  // r^2
   p.l = __fmaf_rn(__fmul_rn(2.0f, r.h), r.l, p.l);
@@ -173,13 +204,27 @@ __device__ __forceinline__ void sincos_tab(const float4 t, ff r, ff& s, ff& c) {
   // sin r = r - r^3/6 (r^3/6 < 6e-10 is exact enough in float: error < 4e-17;
   // r^5/120 < 8e-17 dropped)
   const ff sr = {r.h, __fsub_rn(r.l, __fmul_rn(__fmul_rn(p.h, r.h), 1.0f / 6.0f))};
-  // Every table entry is 0 or at least sin(2pi/2048) = 3.07e-3 in magnitude while
-  // |r| <= pi/2048 = 1.54e-3, so in each sum below the first term is zero or the larger
-  // one: |S|, |C| > |C sr|, |S sr| >= 3.07e-3 |r| > r^2/2 >= |S cm|, |C cm|.
+  // Every entry of the plain table is 0 or at least sin(2pi/2048) = 3.07e-3 in magnitude
+  // while |r| <= pi/2048 = 1.54e-3, so in each sum below the first term is zero or the
+  // larger one: |S|, |C| > |C sr|, |S sr| >= 3.07e-3 |r| > r^2/2 >= |S cm|, |C cm|.  A
+  // common amplitude scales every term alike and keeps the order.
   const ff S = {t.x, t.y}, C = {t.z, t.w};
   const ff Ssr = ff_mul(S, sr), Csr = ff_mul(C, sr);
   s = ff_add_ordered(S, ff_add_ordered(Csr, ff_mul(S, cm)));
   c = ff_add_ordered(C, ff_add_ordered(ff{-Ssr.h, -Ssr.l}, ff_mul(C, cm)));
+}
+
+// The changes of sin and cos from a to a + d, given those at a, |d| <= ~2e-3:
+//   sin(a + d) - sin a = cos a sin d + sin a (cos d - 1)  -> qs
+//   cos(a + d) - cos a = cos a (cos d - 1) - sin a sin d  -> qc
+__device__ __forceinline__ void sincos_delta(ff sa, ff ca, ff d, ff& qs, ff& qc) {
+  ff d2 = two_prod(d.h, d.h);
+  d2.l = __fmaf_rn(__fmul_rn(2.0f, d.h), d.l, d2.l);
+  // cos d - 1 = -d^2/2 + d^4/24;  sin d = d - d^3/6 (d^5/120 < 2e-16 relative, dropped)
+  const ff cmd = {__fmul_rn(-0.5f, d2.h), __fmaf_rn(__fmul_rn(d2.h, d2.h), 1.0f / 24.0f, __fmul_rn(-0.5f, d2.l))};
+  const ff sd = {d.h, __fsub_rn(d.l, __fmul_rn(__fmul_rn(d2.h, d.h), 1.0f / 6.0f))};
+  qs = ff_add(ff_mul(ca, sd), ff_mul(sa, cmd));
+  qc = ff_sub(ff_mul(ca, cmd), ff_mul(sa, sd));
 }
 
 // sin and cos of a + d from those of a, |d| <= ~2e-3.
@@ -200,6 +245,21 @@ __device__ __forceinline__ double wrap_2pi_fast(double x) {
   return x;
 }
 
+// The series of sincos_delta / sincos_shift hold for |delta| <= SOAX_SHIFT_MAX (their first
+// dropped terms, delta^5/120 and delta^6/720, stay below 2.5e-16); a longer shift takes
+// the table at the midpoint itself.
+#define SOAX_SHIFT_MAX 0x1p-9f
+
+// xm = x + (dt/2) v as binary64 (one rounding, as the binary64 arithmetic forms it),
+// reduced into [0, 2pi] for reduce_angle with a two-part 2pi (Cody and Waite).
+__device__ __forceinline__ double far_midpoint(double dt, double x, float v) {
+  double xm = __fma_rn(0.5 * dt, f2d_exact(v), x);
+  const double q = floor(xm * 0x1.45f306dc9c883p-3);  // xm / 2pi
+  xm = __fma_rn(-q, 0x1.921fb54442d18p+2, xm);
+  xm = __fma_rn(-q, 0x1.1a62633145c07p-52, xm);
+  return xm < 0.0 ? xm + SOAX_TWO_PI : xm;
+}
+
 // sin and cos of the three coordinates of x (s0, c0) and of xm = x + (dt/2) v (s1, c1).
 __device__ __forceinline__ void step_trig(const StepC& k, const float4* __restrict__ tab, const double x[3],
                                           const float v[3], ff s0[3], ff c0[3], ff s1[3], ff c1[3]) {
@@ -209,7 +269,12 @@ __device__ __forceinline__ void step_trig(const StepC& k, const float4* __restri
     ff r;
     reduce_angle(x[c], idx, r);
     sincos_tab(tab[idx], r, s0[c], c0[c]);
-    sincos_shift(s0[c], c0[c], ff_mul_f(k.hdt, v[c]), s1[c], c1[c]);
+    if (fabsf(v[c]) <= k.vnear) {
+      sincos_shift(s0[c], c0[c], ff_mul_f(k.hdt, v[c]), s1[c], c1[c]);
+    } else {
+      reduce_angle(far_midpoint(k.dt_d, x[c], v[c]), idx, r);
+      sincos_tab(tab[idx], r, s1[c], c1[c]);
+    }
   }
 }
 
@@ -221,22 +286,41 @@ __device__ __forceinline__ void abc_u(const StepC& k, const ff s[3], const ff c[
 }
 
 // One step: x (binary64 position, in/out), v (f32 velocity, in/out), a2out (the last
-// stage acceleration rounded to f32).  tab: the 2048-entry table (shared memory).
-__device__ __forceinline__ void rk2_step_fast(const StepC& k, const float4* __restrict__ tab, double x[3],
-                                              float v[3], float a2out[3]) {
-  ff s0[3], c0[3], s1[3], c1[3], u0[3], u1[3];
-  step_trig(k, tab, x, v, s0, c0, s1, c1);
-  abc_u(k, s0, c0, u0);
-  abc_u(k, s1, c1, u1);
+// stage acceleration rounded to f32, computed when ACC).  trig gives the amplitude-scaled
+// table entries.  With P_c = a_c sin x_c, Q_c = a_c cos x_c (a = (B, C, A)),
+//   u(x) = (P_z + Q_y, P_x + Q_z, P_y + Q_x),
+// and u(xm) - u(x) is the same combination of the changes dP, dQ over the shift
+// (dt/2) v (sincos_delta), so sin and cos of xm are never formed.  Then, with
+// w0 = u(x) - v, hs = (dt/2)/tau, ds = dt/tau:
+//   vm = v + hs w0,   u(xm) - vm = (1 - hs) w0 + du,   v' = v + ds (u(xm) - vm).
+// RN32(v + t.h + t.l), correctly rounded: v + t.h = s + e exactly (two_sum), e + t.l
+// is rounded to odd (toward zero, last bit set when inexact), and rounding s plus that
+// to nearest gives the rounding of the exact sum (Boldo and Melquiond, rounding to odd:
+// a rounding boundary of s is a short binary fraction, even at the precision of e + t.l,
+// so it can neither equal the odd value nor fall between it and e + t.l).
+__device__ __forceinline__ float round_sum_f32(float v, ff t) {
+  const ff se = two_sum(v, t.h);
+  const float up = __fadd_ru(se.l, t.l), dn = __fadd_rd(se.l, t.l);
+  const float z = fabsf(up) < fabsf(dn) ? up : dn;
+  const float odd = __uint_as_float(__float_as_uint(z) | (up != dn ? 1u : 0u));
+  return __fadd_rn(se.h, odd);
+}
+
+// The update from u(x) - v = w0 and du = u(xm) - u(x) (shared by the two paths below).
+template <bool ACC>
+__device__ __forceinline__ void rk2_update(const StepC& k, const ff u0[3], const ff du[3], double x[3], float v[3],
+                                           float a2out[3]) {
   float vn[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const ff a1 = ff_mul(ff_add_f(u0[c], -v[c]), k.s);
-    const ff vm = ff_add_f(ff_mul(k.hdt, a1), v[c]);
-    const ff a2 = ff_mul(ff_sub(u1[c], vm), k.s);
-    const ff nv = ff_add_f(ff_mul(k.dt, a2), v[c]);
-    vn[c] = __fadd_rn(nv.h, nv.l);
-    a2out[c] = __fadd_rn(a2.h, a2.l);
+    const ff w0 = ff_add_f(u0[c], -v[c]);
+    const ff vm = ff_add_f(ff_mul(k.hs, w0), v[c]);
+    const ff w1 = ff_add(ff_mul(k.gh, w0), du[c]);  // u(xm) - vm
+    vn[c] = round_sum_f32(v[c], ff_mul(k.ds, w1));
+    if constexpr (ACC) {
+      const ff a2 = ff_mul(k.s, w1);
+      a2out[c] = __fadd_rn(a2.h, a2.l);
+    }
     double xn = __fma_rn(k.dt_d, f2d_exact(vm.h), x[c]);
     xn = __fma_rn(k.dt_d, f2d_exact(vm.l), xn);
     x[c] = wrap_2pi_fast(xn);
@@ -244,6 +328,40 @@ __device__ __forceinline__ void rk2_step_fast(const StepC& k, const float4* __re
   v[0] = vn[0];
   v[1] = vn[1];
   v[2] = vn[2];
+}
+
+// True when every component of v is short enough for the shift series: |v_c| <= vnear
+// = SOAX_SHIFT_MAX / (dt/2).  The same test picks each coordinate's path below, so a
+// particle gets the same bits whether its group took the NEAR path or not.
+__device__ __forceinline__ bool near_shift(const StepC& k, const float v[3]) {
+  return fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))) <= k.vnear;
+}
+
+// NEAR: the caller has checked near_shift (straight-line code); otherwise each
+// coordinate takes the series or, for a long shift, the table at the midpoint itself.
+template <bool ACC, bool NEAR, class Trig>
+__device__ __forceinline__ void rk2_step_fast(const StepC& k, const Trig& trig, double x[3], float v[3],
+                                              float a2out[3]) {
+  ff P[3], Q[3], dP[3], dQ[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    int idx;
+    ff r;
+    reduce_angle(x[c], idx, r);
+    sincos_tab(trig(c, idx), r, P[c], Q[c]);
+    if (NEAR || fabsf(v[c]) <= k.vnear) {
+      sincos_delta(P[c], Q[c], ff_mul_f(k.hdt, v[c]), dP[c], dQ[c]);
+    } else {
+      ff P1, Q1;
+      reduce_angle(far_midpoint(k.dt_d, x[c], v[c]), idx, r);
+      sincos_tab(trig(c, idx), r, P1, Q1);
+      dP[c] = ff_sub(P1, P[c]);
+      dQ[c] = ff_sub(Q1, Q[c]);
+    }
+  }
+  const ff u0[3] = {ff_add(P[2], Q[1]), ff_add(P[0], Q[2]), ff_add(P[1], Q[0])};
+  const ff du[3] = {ff_add(dP[2], dQ[1]), ff_add(dP[0], dQ[2]), ff_add(dP[1], dQ[0])};
+  rk2_update<ACC>(k, u0, du, x, v, a2out);
 }
 
 // xb += J(x)^T ub and th[0..2] += (du/d(A, B, C))^T ub at the point whose sines and
@@ -314,6 +432,19 @@ static __device__ const float4 kTrigTable[SOAX_TRIG_TABLE_SIZE] = {SOAX_TRIG_TAB
 // Copy the table (32 KB) into shared memory (every thread of the block must call this).
 __device__ __forceinline__ void load_trig_table(float4* s_tab) {
   for (int i = threadIdx.x; i < SOAX_TRIG_TABLE_SIZE; i += blockDim.x) s_tab[i] = kTrigTable[i];
+  __syncthreads();
+}
+
+constexpr int kScaledTrigBytes = 3 * SOAX_TRIG_TABLE_SIZE * 16;  // 96 KB
+
+// Fill the three amplitude-scaled tables (x with B, y with C, z with A) in shared memory
+// (every thread of the block must call this).
+__device__ __forceinline__ void load_scaled_trig_tables(float4* s_tab, ff A, ff B, ff C) {
+  for (int i = threadIdx.x; i < 3 * SOAX_TRIG_TABLE_SIZE; i += blockDim.x) {
+    const int c = i / SOAX_TRIG_TABLE_SIZE;
+    const ff amp = c == 0 ? B : (c == 1 ? C : A);
+    s_tab[i] = scale_entry(amp, kTrigTable[i - c * SOAX_TRIG_TABLE_SIZE]);
+  }
   __syncthreads();
 }
 

@@ -4,8 +4,9 @@
 #include "rk2_fast.cuh"
 
 namespace soax {
-__device__ __forceinline__ void rk2_step(const StepC& k, const float4* __restrict__ tab, double x[3], float v[3],
-                                         float a2out[3]) {
-  rk2_step_fast(k, tab, x, v, a2out);
+// One particle, either path (see near_shift).
+template <bool ACC, class Trig>
+__device__ __forceinline__ void rk2_step(const StepC& k, const Trig& trig, double x[3], float v[3], float a2out[3]) {
+  rk2_step_fast<ACC, false>(k, trig, x, v, a2out);
 }
 }  // namespace soax

@@ -1,5 +1,6 @@
 // soax_step (SoA) and soax_step_aos: one pass over memory per midpoint-RK2 step.
 #include <cmath>
+#include <mutex>
 
 #include "soax_internal.h"
 #include "step_core.cuh"
@@ -91,20 +92,46 @@ constexpr int kStepPPT = 2;
 constexpr int kStepBlock = 512;
 constexpr int kStepMinBlocks = 2;
 
+template <int PPT, int VB, bool TAU, bool ACC>
+__device__ __forceinline__ void step_soa_loop(const EnsArgs& e, const StepC& kc, const TrigScaled& tg) {
+  const int64_t ngroups = (e.n + PPT - 1) / PPT;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x)
+    step_span_t<PPT, VB, TAU, ACC>(e, kc, tg, g * PPT, e.n - g * PPT, 1);
+}
+
 // Persistent: a grid that fills the GPU once walks groups of PPT particles with a
-// fixed stride, so each block copies the sin/cos table into shared memory only once.
+// fixed stride, so each block builds its amplitude-scaled tables (96 KB of dynamic
+// shared memory) only once.
 template <int PPT, int VB>
 __global__ void __launch_bounds__(kStepBlock, kStepMinBlocks) k_step_soa(EnsArgs e, FlowK f) {
-  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
-  load_trig_table(s_tab);
-  const int64_t ngroups = (e.n + PPT - 1) / PPT;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i0 = g * PPT;
-    if (i0 + PPT <= e.n)
-      step_group<PPT, VB>(e, f, s_tab, i0, 1);
-    else
-      step_tail(e, f, s_tab, i0, (int)(e.n - i0), 1);
+  extern __shared__ float4 s_tab3[];
+  load_scaled_trig_tables(s_tab3, ff_from2(e.Af), ff_from2(e.Bf), ff_from2(e.Cf));
+  const StepC kc = make_stepc(e, f);
+  const TrigScaled tg{s_tab3};
+  if (e.tau_src) {
+    if (e.ax) step_soa_loop<PPT, VB, true, true>(e, kc, tg);
+    else step_soa_loop<PPT, VB, true, false>(e, kc, tg);
+  } else {
+    if (e.ax) step_soa_loop<PPT, VB, false, true>(e, kc, tg);
+    else step_soa_loop<PPT, VB, false, false>(e, kc, tg);
   }
+}
+
+// Dynamic shared memory above 48 KB and the largest carveout, set once per device.
+static int prepare_step_kernel() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail(cudaGetLastError(), "soax_step: device");
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return SOAX_OK;
+  const void* fn = (const void*)k_step_soa<kStepPPT, 128>;
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kScaledTrigBytes);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (err != cudaSuccess) return cuda_fail(err, "soax_step: kernel attributes");
+  done[dev] = true;
+  return SOAX_OK;
 }
 
 struct AosArgs {
@@ -114,33 +141,37 @@ struct AosArgs {
   EnsArgs e;  // flow amplitudes and tau (the plane pointers are unused)
 };
 
+template <bool ACC>
+__device__ __forceinline__ void step_aos_loop(const AosArgs& a, const StepC& kc, const TrigUnscaled& tg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    char* r = a.rec + i * a.R;
+    const double* pp = reinterpret_cast<const double*>(r + a.pos_off);
+    const float* vp = reinterpret_cast<const float*>(r + a.vel_off);
+    double p[3] = {pp[0], pp[1], pp[2]};
+    float v[3] = {vp[0], vp[1], vp[2]}, acc[3];
+    StepC k = kc;
+    if (a.tau_off >= 0) set_inv_tau(k, ff_inv_tau(a.e.tsf, *reinterpret_cast<const float*>(r + a.tau_off)));
+    rk2_step<ACC>(k, tg, p, v, acc);
+    double* pw = reinterpret_cast<double*>(r + a.pos_off);
+    float* vw = reinterpret_cast<float*>(r + a.vel_off);
+    pw[0] = p[0]; pw[1] = p[1]; pw[2] = p[2];
+    vw[0] = v[0]; vw[1] = v[1]; vw[2] = v[2];
+    if constexpr (ACC) {
+      float* aw = reinterpret_cast<float*>(r + a.acc_off);
+      aw[0] = acc[0]; aw[1] = acc[1]; aw[2] = acc[2];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_step_aos(AosArgs a, FlowK f) {
   __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
   load_trig_table(s_tab);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-  char* r = a.rec + i * a.R;
-  const double* pp = reinterpret_cast<const double*>(r + a.pos_off);
-  const float* vp = reinterpret_cast<const float*>(r + a.vel_off);
-  double p[3] = {pp[0], pp[1], pp[2]};
-  float v[3] = {vp[0], vp[1], vp[2]}, acc[3];
-  StepC k;
-  k.A = ff_from2(a.e.Af);
-  k.B = ff_from2(a.e.Bf);
-  k.C = ff_from2(a.e.Cf);
-  k.dt = ff_from2(f.dtf);
-  k.hdt = ff_from2(f.hdtf);
-  k.dt_d = f.dt;
-  k.s = a.tau_off >= 0 ? ff_inv_tau(a.e.tsf, *reinterpret_cast<const float*>(r + a.tau_off)) : ff_from2(a.e.itf);
-  rk2_step(k, s_tab, p, v, acc);
-  double* pw = reinterpret_cast<double*>(r + a.pos_off);
-  float* vw = reinterpret_cast<float*>(r + a.vel_off);
-  pw[0] = p[0]; pw[1] = p[1]; pw[2] = p[2];
-  vw[0] = v[0]; vw[1] = v[1]; vw[2] = v[2];
-  if (a.acc_off >= 0) {
-    float* aw = reinterpret_cast<float*>(r + a.acc_off);
-    aw[0] = acc[0]; aw[1] = acc[1]; aw[2] = acc[2];
-  }
-  }
+  const StepC kc = make_stepc(a.e, f);
+  const TrigUnscaled tg = trig_unscaled(s_tab, a.e);
+  if (a.acc_off >= 0)
+    step_aos_loop<true>(a, kc, tg);
+  else
+    step_aos_loop<false>(a, kc, tg);
 }
 
 }  // namespace soax
@@ -154,11 +185,12 @@ extern "C" int soax_step(soax_t h, const soax_flow* fl, int32_t nsteps, void* st
   FlowK f;
   if (int r = make_ens_args(h, fl, h->current, &e, &f, "soax_step")) return r;
   if (h->n == 0 || nsteps == 0) return SOAX_OK;
-  const int grid = persistent_grid((const void*)k_step_soa<kStepPPT, 128>, kStepBlock, 0,
+  if (int r = prepare_step_kernel()) return r;
+  const int grid = persistent_grid((const void*)k_step_soa<kStepPPT, 128>, kStepBlock, kScaledTrigBytes,
                                    grid_for((h->n + kStepPPT - 1) / kStepPPT, kStepBlock));
   cudaStream_t s = as_stream(stream);
   for (int k = 0; k < nsteps; ++k) {
-    k_step_soa<kStepPPT, 128><<<grid, kStepBlock, 0, s>>>(e, f);
+    k_step_soa<kStepPPT, 128><<<grid, kStepBlock, kScaledTrigBytes, s>>>(e, f);
     if (int r = check_launch("soax_step")) return r;
   }
   return SOAX_OK;

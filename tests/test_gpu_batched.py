@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 SCHEMA = sx.BASIC_SCHEMA
 
 
-def _ensembles(sizes, seed=0):
+def _ensembles(sizes, seed=0, dt=1e-3):
     rng = np.random.default_rng(seed)
     parts, flows = [], []
     for e, n in enumerate(sizes):
@@ -20,7 +20,7 @@ def _ensembles(sizes, seed=0):
         p.load(soax_inputs.ensemble_set(e, n))
         parts.append(p)
         a, b, c = rng.uniform(0.5, 1.5, 3)
-        flows.append(sx.Flow(A=a, B=b, C=c, tau=rng.uniform(0.01, 1.0), dt=1e-3))
+        flows.append(sx.Flow(A=a, B=b, C=c, tau=rng.uniform(0.01, 1.0), dt=dt))
     return parts, flows
 
 
@@ -44,6 +44,21 @@ def test_batched_equals_plain_for_every_shape():
                     parts, _ = _ensembles(SIZES)
                     sx.step_batched(parts, flows, steps, sx.Tune(ppt, block, vb, fuse))
                     assert _bytes(parts) == want, (ppt, vb, block, fuse)
+
+
+def test_batched_equals_plain_with_long_shifts():
+    """dt = 0.05: groups mix the shift series and the table at the midpoint (and tau as
+    short as 0.01 gives dt/tau up to 5); the per-coordinate choice keeps the bits equal."""
+    steps = 4
+    ref, flows = _ensembles(SIZES, 5, dt=0.05)
+    for p, f in zip(ref, flows):
+        p.step(f, steps)
+    want = _bytes(ref)
+    for ppt in (1, 2, 4):
+        for fuse in (0, 1):
+            parts, _ = _ensembles(SIZES, 5, dt=0.05)
+            sx.step_batched(parts, flows, steps, sx.Tune(ppt, 256, 128, fuse))
+            assert _bytes(parts) == want, (ppt, fuse)
 
 
 def test_batched_repeated_calls_and_graph_capture():

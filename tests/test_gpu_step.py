@@ -48,13 +48,14 @@ def test_zero_steps_and_empty():
     assert all(np.array_equal(a, b) for a, b in zip(q.numpy()["pos"], d["pos"]))
 
 
-def test_aos_step_bit_equal_to_soa():
+@pytest.mark.parametrize("dt", [1e-3, 0.02])
+def test_aos_step_bit_equal_to_soa(dt):
     n = 50001
     d = soax_inputs.basic_set(n, 3)
     p = sx.Particles(sx.BASIC_SCHEMA, n)
     p.load(d)
     aos = p.to_aos()
-    f = sx.Flow()
+    f = sx.Flow(tau=0.2, dt=dt)
     p.step(f, 7)
     p.step_aos(aos, f, 7)
     q = sx.Particles(sx.BASIC_SCHEMA, n)
@@ -145,4 +146,14 @@ def test_step_amplitudes_and_stiff_tau(A, B, C, tau, dt):
     """Non-unit amplitudes and dt/tau up to 0.1, the range of the batched workload."""
     n, steps = 20001, 100
     d, g, opos, ovel = _run_both(n, steps, A, B, C, tau, dt, seed=int(tau * 1000))
+    assert_parity(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], np.full(n, tau), A, B, C, dt, steps)
+
+
+@pytest.mark.parametrize("A,B,C,tau,dt,steps", [(1.3, 0.8, 1.1, 0.2, 0.02, 30), (1.0, 1.0, 1.0, 5.0, 0.5, 8)])
+def test_step_long_shifts(A, B, C, tau, dt, steps):
+    """Steps long enough that the half-step shift (dt/2)|v| leaves the range of the shift
+    series for some coordinates (and, at dt = 0.5, carries midpoints across the periodic
+    boundary): those coordinates take the table at the midpoint itself."""
+    n = 20001
+    d, g, opos, ovel = _run_both(n, steps, A, B, C, tau, dt, seed=77)
     assert_parity(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], np.full(n, tau), A, B, C, dt, steps)
