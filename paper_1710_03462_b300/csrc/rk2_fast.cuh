@@ -10,8 +10,8 @@
 // evaluated to binary64 accuracy without the FP64 pipe for the trigonometry and the
 // velocity arithmetic.
 //
-// B300 executes FP64 at a small fraction of its FP32 and integer rates (measured: about
-// 1.6 FP64 FMA per SM per clock against ~110 FP32 FMA), and a native binary64 sincos
+// B300 executes FP64 at a small fraction of its FP32 and integer rates (measured: one to
+// 1.6 FP64 FMA lanes per SM per clock against ~124 FP32 FMA lanes), and a native binary64 sincos
 // costs ~25 FP64 instructions; the native step is therefore bound by the FP64 pipe at a
 // few percent of HBM bandwidth.  Here:
 //
@@ -24,16 +24,19 @@
 //    the rest is the residual r = x - theta_k (|r| <= pi/2048) as a float pair; then
 //    sin(theta_k + r) = S + (C sin r + S (cos r - 1)) with short Taylor series for the
 //    residual (a table-driven method in the manner of Tang);
-//  * sin/cos of the midpoint xm = x + (dt/2) v come from those of x by the angle
-//    addition formula with delta = (dt/2) v (|delta| <= ~2e-3);
-//  * the new velocity v + dt a2 is rounded to f32 from the float pair with one IEEE add
-//    (correct rounding of hi + lo); the new position is x + dt vm with vm = vm_hi + vm_lo
+//  * each coordinate enters u with one amplitude (x with B, y with C, z with A), so the
+//    table entries are read pre-scaled (P = a sin, Q = a cos), and u(xm) - u(x) is the
+//    same combination of the changes of P and Q over the shift delta = (dt/2) v from the
+//    angle addition formula (|delta| <= 2^-9; longer shifts take the table at xm);
+//  * the new velocity v + dt a2 is rounded to f32 from the float pair correctly (rounding
+//    to odd, round_sum_f32); the new position is x + dt vm with vm = vm_hi + vm_lo
 //    applied as two binary64 FMAs (the only FP64 instructions of the step).
 //
-// Accuracy (checked against the CPU oracle by the parity tests): sin/cos to ~4e-15
-// absolute (the 2^-48 precision of a float pair); the flow enters v' scaled by
-// dt/tau <= 0.1, so velocities before their f32 rounding are within ~1e-16 relative of
-// binary64 arithmetic, and positions within about one binary64 ulp per step.
+// Accuracy (checked against the CPU oracle by the parity tests and against a long-double
+// evaluation of the step on the host): sin/cos to ~5e-15 absolute (the 2^-48 precision
+// of a float pair); the flow enters v' scaled by dt/tau, so at dt/tau = 0.01 the velocity
+// before its f32 rounding is within ~1.2e-15 absolute (rms 1e-16) of the exact step, and
+// positions are within about one binary64 ulp per step.
 #pragma once
 #include <cstdint>
 
