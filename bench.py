@@ -5,13 +5,18 @@
 
 Workload (one "step" of this benchmark): the 16,777,216-particle set {i32 id, f64 pos[3],
 f32 vel[3]} in the ABC flow (A = B = C = 1, tau = 0.1, dt = 1e-3); one bench step is one
-sort interval: 10 midpoint-RK2 steps (one launch and one pass over the planes each)
-followed by the cell sort on a 32^3 grid (keys, stable radix sort, permute-gather of every
-plane).  K bench steps = 10 K RK2 steps; the default K = 100 is the full 1000-step run.
+sort interval: 10 midpoint-RK2 steps in one pass over the planes (soax_step_fused: each
+particle loaded once, advanced 10 steps in registers, stored once) followed by the cell
+sort on a 32^3 grid (keys, stable radix sort, permute-gather of every plane).  K bench
+steps = 10 K RK2 steps; the default K = 100 is the full 1000-step run.
 
-Metric: particle-steps/s (whole job, all ranks).  The dominant kernel is the RK2 step; its
-roofline is HBM bandwidth at 72 algorithmic bytes per particle-step (pos 24 + vel 12 bytes
-read and written), against the measured copy bandwidth in MEASURED_PEAKS.json.
+Metric: particle-steps/s (whole job, all ranks).  The dominant kernel is the fused step;
+with the planes moved once per 10 steps it is bound by instruction issue, not by HBM.  Its
+roofline is the issue rate, one warp-instruction per clock per SM sub-partition (4 per SM,
+148 SMs, 32 lanes, 2032 MHz: 38.5 T thread-instructions/s), against the instructions per
+particle-step that ncu counts for the current sources (profiles/ncu_traffic.json).  The
+one-pass-per-step kernel (soax_step, 72 algorithmic bytes per particle-step against the
+measured copy bandwidth in MEASURED_PEAKS.json) is timed as a secondary row.
 
 Also measured in the same run ("rows"): the AoS <-> SoA round trip and the AoS step on the
 same set, the sort's share, the forward+adjoint of the 1M-particle K = 1000 problem against
@@ -47,6 +52,10 @@ RK2_PER_STEP = WL["sort_every"]
 BYTES_PER_PARTICLE_STEP = 72  # pos 3 x f64 + vel 3 x f32, read and written
 METRIC = "particle-steps/s"
 L2_BYTES = 126 * 2 ** 20
+# Issue-rate peak of B300: 1 warp-instruction per clock per SM sub-partition, 4 per SM,
+# 148 SMs, 32 lanes, at the 2032 MHz maximum SM clock (thread-instructions per second).
+SMSP_PER_SM = 4
+MAX_SM_MHZ = 2032.0
 
 
 def parse_args(argv=None):
@@ -95,19 +104,28 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of kernel from the committed ncu summary, if it was taken on
-    the current sources; else None."""
+def ncu_record(kernel):
+    """The committed ncu figures of kernel (profiles/ncu_traffic.json) if they were taken
+    on the current sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             j = json.load(fh)
         e = j.get(kernel)
         if e and e.get("source_hash") == source_hash():
-            return float(e["dram_bytes_per_launch_full_size"])
+            return e
     except (OSError, ValueError, KeyError, TypeError):
         pass
     return None
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per full-size launch of kernel from the committed ncu record, or None."""
+    e = ncu_record(kernel)
+    try:
+        return float(e["dram_bytes_per_launch_full_size"]) if e else None
+    except (KeyError, TypeError, ValueError):
+        return None
 
 
 class ClockSampler:
@@ -242,24 +260,19 @@ def run_soax(args):
     stream = torch.cuda.current_stream(dev)
 
     def bench_step(ev=None):
-        for k in range(RK2_PER_STEP):
-            if ev is not None:
-                ev[0][k].record(stream)
-            p.step(flow, 1)
-            if ev is not None:
-                ev[1][k].record(stream)
         if ev is not None:
-            ev[2].record(stream)
+            ev[0].record(stream)
+        p.step_fused(flow, RK2_PER_STEP)
+        if ev is not None:
+            ev[1].record(stream)
         p.sort_by_cell(WL["grid"], ws)
         if ev is not None:
-            ev[3].record(stream)
+            ev[2].record(stream)
 
     for _ in range(args.warmup):
         bench_step()
     torch.cuda.synchronize(dev)
-    evs = [([torch.cuda.Event(enable_timing=True) for _ in range(RK2_PER_STEP)],
-            [torch.cuda.Event(enable_timing=True) for _ in range(RK2_PER_STEP)],
-            torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
@@ -273,8 +286,8 @@ def run_soax(args):
     if world > 1:
         dist.barrier()
     elapsed = start.elapsed_time(stop) / 1e3
-    step_ms = [evs[s][0][k].elapsed_time(evs[s][1][k]) for s in range(args.steps) for k in range(RK2_PER_STEP)]
-    sort_ms = [evs[s][2].elapsed_time(evs[s][3]) for s in range(args.steps)]
+    fused_ms = [evs[s][0].elapsed_time(evs[s][1]) for s in range(args.steps)]
+    sort_ms = [evs[s][1].elapsed_time(evs[s][2]) for s in range(args.steps)]
     units = n * RK2_PER_STEP * args.steps
     tot_units, max_el = aggregate(units, elapsed, dev)
 
@@ -302,9 +315,12 @@ def run_soax(args):
         if world > 1:
             dist.destroy_process_group()
         return 0
-    peak, peak_kind = measured_peaks()
-    step_avg_s = statistics.mean(step_ms) / 1e3
-    achieved = BYTES_PER_PARTICLE_STEP * n / step_avg_s / 1e9
+    fused_s = statistics.mean(fused_ms) / 1e3
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_inst = sms * SMSP_PER_SM * 32 * MAX_SM_MHZ * 1e6 / 1e12  # T thread-instructions/s
+    rec = ncu_record("k_step_soa_fused")
+    inst = float(rec["inst_per_particle_step"]) if rec and "inst_per_particle_step" in rec else None
+    achieved = inst * n * RK2_PER_STEP / fused_s / 1e12 if inst else None
     sort_launches = 1 + 3 * 2 + 1  # keys, (upsweep, scan, downsweep) x 2 passes, permute
     line = {
         "metric": METRIC, "value": tot_units / max_el, "unit": "particle-steps/s", "n_gpus": world,
@@ -314,14 +330,18 @@ def run_soax(args):
                    "rk2_steps_per_step": RK2_PER_STEP, "grid": WL["grid"], "flow": "ABC A=B=C=1 tau=0.1 dt=1e-3",
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 ({n * 40 / 2**20:.0f} MiB of planes > 126 MiB)"},
-        "roofline": {"bound": "hbm", "kernel": "k_step_soa", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
-                     "bytes_per_unit": BYTES_PER_PARTICLE_STEP, "units_per_launch": n,
-                     "traffic": ncu_traffic("k_step_soa"), "launch_ms": statistics.mean(step_ms)},
+        "roofline": {"bound": "alu", "kernel": "k_step_soa_fused", "achieved": achieved, "peak": peak_inst,
+                     "unit": "Tinst/s", "frac": achieved / peak_inst if achieved else None,
+                     "peak_kind": f"issue rate: 1 warp-instruction/clock per SM sub-partition x {SMSP_PER_SM} x "
+                                  f"{sms} SMs x 32 lanes at {MAX_SM_MHZ:.0f} MHz",
+                     "work_per_unit": inst, "work_unit": "thread-instructions per particle-step (ncu counter)",
+                     "units_per_launch": n * RK2_PER_STEP, "traffic": ncu_traffic("k_step_soa_fused"),
+                     "hbm_GB/s": BYTES_PER_PARTICLE_STEP * n / fused_s / 1e9,
+                     "launch_ms": statistics.mean(fused_ms)},
         "sort_ms": statistics.mean(sort_ms),
         "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d, "steps": e2e_steps},
-        "gpu_launches": args.steps * (RK2_PER_STEP + sort_launches),
+        "gpu_launches": args.steps * (1 + sort_launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu_baseline(n) if world == 1 or rank == 0 else None,
         "rows": rows,
@@ -376,6 +396,15 @@ def secondary_rows(sx, torch, p, d, dev):
     n = p.n
     flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
     rows["euler_replica"] = euler_replica(sx, torch, n, dev)
+    # The one-pass-per-step kernel (soax_step): HBM roofline at 72 bytes per particle-step.
+    peak, peak_kind = measured_peaks()
+    t1 = _time(torch, lambda: p.step(flow, 1), reps=10)
+    tf = _time(torch, lambda: p.step_fused(flow, RK2_PER_STEP), reps=3)
+    rows["step_one_pass"] = {"kernel": "k_step_soa", "launch_ms": t1 * 1e3, "particle-steps/s": n / t1,
+                             "bound": "hbm", "achieved_GB/s": BYTES_PER_PARTICLE_STEP * n / t1 / 1e9, "peak_GB/s": peak,
+                             "frac": BYTES_PER_PARTICLE_STEP * n / t1 / 1e9 / peak, "peak_kind": f"{peak_kind} copy",
+                             "traffic": ncu_traffic("k_step_soa"),
+                             "fused_over_one_pass": t1 * RK2_PER_STEP / tf}
     # AoS <-> SoA round trip (176 algorithmic bytes per particle) and the AoS step (96).
     aos = p.to_aos()
     t_rt = _time(torch, lambda: (p.to_aos(aos), p.from_aos(aos)), reps=5)

@@ -174,6 +174,19 @@ int soax_remove(soax_t h, const uint32_t* idx, int64_t k, void* ws, size_t ws_by
  * step; each step is one kernel launch (capturable in a CUDA graph). */
 int soax_step(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream);
 
+/* The same nsteps (>= 0) midpoint-RK2 steps as soax_step in ONE pass over the planes:
+ * each particle is loaded once, advanced nsteps steps in registers and stored once, so
+ * the planes move once per call instead of once per step (one kernel launch).  The
+ * velocity arithmetic is soax_step's, including the f32 rounding of v after every step.
+ * Between steps the position is held as a 64-bit fixed-point fraction of a turn,
+ * frac(x / 2pi) 2^64 (resolution 2^-64 turn = 3.4e-19 rad, finer than binary64 at
+ * x >= 2^-8), instead of being rounded to binary64 every step; it is rounded to binary64
+ * once at the end, wrapped into [0, 2pi).  Results therefore agree with soax_step to
+ * within a few binary64 ulps per step, not bit for bit.  Positions on entry must lie in
+ * [0, 8) (soax_step's output always does).  Tau and acceleration fields as for
+ * soax_step; acc receives the last step's a2. */
+int soax_step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream);
+
 /* The same step, bit-identical per particle, on AoS records in place (layout from
  * soax_aos_layout; the flow's field indices refer to this handle's schema). */
 int soax_step_aos(soax_t h, void* aos_dev, const soax_flow* fl, int32_t nsteps, void* stream);

@@ -190,6 +190,11 @@ class Particles:
         fl = self.flow(f)
         _check(lib().soax_step(self.h, C.byref(fl), int(nsteps), _stream(stream)), "soax_step")
 
+    def step_fused(self, f: Flow, nsteps=1, stream=None):
+        """nsteps steps in one pass over the planes (soax_step_fused)."""
+        fl = self.flow(f)
+        _check(lib().soax_step_fused(self.h, C.byref(fl), int(nsteps), _stream(stream)), "soax_step_fused")
+
     def aos_layout(self):
         rb = C.c_int64()
         offs = (C.c_int64 * len(self.schema))()

@@ -47,6 +47,7 @@ SIGNATURES = {
     "soax_remove_workspace_bytes": [_i64, _P(_sz)],
     "soax_remove": [_p, _p, _i64, _p, _sz, _p],
     "soax_step": [_p, _P(soax_flow), _i32, _p],
+    "soax_step_fused": [_p, _P(soax_flow), _i32, _p],
     "soax_step_aos": [_p, _p, _P(soax_flow), _i32, _p],
     "soax_cell_keys": [_p, _i32, _i32, _p, _p],
     "soax_radix_workspace_bytes": [_i64, _i32, _P(_sz)],

@@ -150,8 +150,9 @@ __device__ __forceinline__ void set_inv_tau(StepC& k, ff s) {
   k.gh = ff_add_f(ff{-k.hs.h, -k.hs.l}, 1.0f);
 }
 
-// x (binary64, 0 <= x < 8) -> table index k and residual r = x - 2 pi k / 2048.
-__device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) {
+// frac(x / 2pi) 2^64 for a binary64 x with 0 <= x < 8: the position as a 64-bit
+// fixed-point fraction of a turn (within 3 units of 2^-64 turn).
+__device__ __forceinline__ uint64_t to_turns(double x) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
   const int e = (int)((hi >> 20) & 0x7FFu);
   const uint64_t m = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
@@ -162,7 +163,12 @@ __device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) {
   else
     X = sh > -64 ? (m >> -sh) : 0ull;  // bits below 2^-61 dropped (< 5e-19)
   // T = X (4/pi) 2^-63 = frac(x / 2pi) 2^64 (within 3 units of the last place).
-  const uint64_t T = __umul64hi(X, SOAX_FOUR_OVER_PI_2P63) << 1;
+  return __umul64hi(X, SOAX_FOUR_OVER_PI_2P63) << 1;
+}
+
+// Angle T (2^-64 turns) -> table index k and residual r = 2 pi T 2^-64 - 2 pi k / 2048
+// in radians (|r| <= pi/2048) as a float pair.
+__device__ __forceinline__ void turns_angle(uint64_t T, int& k, ff& r) {
   const uint64_t U = T + (1ull << 52);
   k = (int)(U >> 53) & (SOAX_TRIG_TABLE_SIZE - 1);
   // rho = U mod 2^53 = residual + 2^52 in 2^-64 turns, 0 <= rho < 2^53.  Its bits 30..52
@@ -176,6 +182,9 @@ __device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) {
   const ff rt = {fhi, flo};
   r = ff_mul(rt, ff{SOAX_TWO_PI_2M64_HI, SOAX_TWO_PI_2M64_LO});
 }
+
+// x (binary64, 0 <= x < 8) -> table index k and residual r = x - 2 pi k / 2048.
+__device__ __forceinline__ void reduce_angle(double x, int& k, ff& r) { turns_angle(to_turns(x), k, r); }
 
 // amp times the table entry t = (sin, cos) as float pairs, packed like the entry.
 __device__ __forceinline__ float4 scale_entry(ff amp, float4 t) {

@@ -1,0 +1,127 @@
+// Kernel template of soax_step_fused: each thread loads groups of PPT particles once,
+// advances them nsteps midpoint-RK2 steps in registers (positions as 64-bit fixed-point
+// turns, rk2_turns.cuh) and stores them once.
+#pragma once
+#include <cstdint>
+
+#include "rk2_turns.cuh"
+#include "step_core.cuh"
+
+namespace soax {
+
+// nsteps steps of one particle (the ragged tail of a launch).  Same per-particle
+// function as fused_group, so a particle gets the same bits on either path.
+template <bool TAU, bool ACC, class Trig>
+__device__ __forceinline__ void fused_tail(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const Trig& trig,
+                                           int64_t i0, int cnt, int nsteps) {
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t i = i0 + j;
+    uint64_t T[3] = {to_turns(e.px[i]), to_turns(e.py[i]), to_turns(e.pz[i])};
+    float v[3] = {e.vx[i], e.vy[i], e.vz[i]}, a[3] = {0.f, 0.f, 0.f};
+    StepC k = kc;
+    if constexpr (TAU) set_inv_tau(k, particle_inv_tau<true>(e, i));
+    for (int s = 0; s < nsteps; ++s) rk2_step_turns<ACC, false>(k, tk, trig, T, v, a);
+    e.px[i] = turns_to_x(T[0]);
+    e.py[i] = turns_to_x(T[1]);
+    e.pz[i] = turns_to_x(T[2]);
+    e.vx[i] = v[0]; e.vy[i] = v[1]; e.vz[i] = v[2];
+    if constexpr (ACC) { e.ax[i] = a[0]; e.ay[i] = a[1]; e.az[i] = a[2]; }
+  }
+}
+
+// The PPT particles i0..i0+PPT-1 (all < n): one vectorised load and store of each plane,
+// nsteps steps in between (nsteps >= 1).  A group whose speeds are all within the shift
+// series (near_shift) runs straight-line code for that step.
+template <int PPT, bool TAU, bool ACC, class Trig>
+__device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const Trig& trig,
+                                            int64_t i0, int nsteps) {
+  double x[PPT], y[PPT], z[PPT];
+  float vx[PPT], vy[PPT], vz[PPT];
+  load_f64<PPT, 128>(e.px, i0, x);
+  load_f64<PPT, 128>(e.py, i0, y);
+  load_f64<PPT, 128>(e.pz, i0, z);
+  load_f32<PPT, 128>(e.vx, i0, vx);
+  load_f32<PPT, 128>(e.vy, i0, vy);
+  load_f32<PPT, 128>(e.vz, i0, vz);
+  uint64_t T[PPT][3];
+  float v[PPT][3], a[PPT][3];
+  ff sj[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    T[j][0] = to_turns(x[j]);
+    T[j][1] = to_turns(y[j]);
+    T[j][2] = to_turns(z[j]);
+    v[j][0] = vx[j]; v[j][1] = vy[j]; v[j][2] = vz[j];
+    if constexpr (TAU) sj[j] = particle_inv_tau<true>(e, i0 + j);
+  }
+  StepC k = kc;
+  for (int s = 0; s < nsteps; ++s) {
+    bool near = true;
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) near = near && near_shift(k, v[j]);
+    if (near) {
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        if constexpr (TAU) set_inv_tau(k, sj[j]);
+        rk2_step_turns<ACC, true>(k, tk, trig, T[j], v[j], a[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        if constexpr (TAU) set_inv_tau(k, sj[j]);
+        rk2_step_turns<ACC, false>(k, tk, trig, T[j], v[j], a[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    x[j] = turns_to_x(T[j][0]);
+    y[j] = turns_to_x(T[j][1]);
+    z[j] = turns_to_x(T[j][2]);
+    vx[j] = v[j][0]; vy[j] = v[j][1]; vz[j] = v[j][2];
+  }
+  store_f64<PPT, 128>(e.px, i0, x);
+  store_f64<PPT, 128>(e.py, i0, y);
+  store_f64<PPT, 128>(e.pz, i0, z);
+  store_f32<PPT, 128>(e.vx, i0, vx);
+  store_f32<PPT, 128>(e.vy, i0, vy);
+  store_f32<PPT, 128>(e.vz, i0, vz);
+  if constexpr (ACC) {
+    float o[PPT];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) o[j] = a[j][c];
+      store_f32<PPT, 128>(c == 0 ? e.ax : (c == 1 ? e.ay : e.az), i0, o);
+    }
+  }
+}
+
+template <int PPT, bool TAU, bool ACC>
+__device__ __forceinline__ void fused_loop(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const TrigScaled& tg,
+                                           int nsteps) {
+  const int64_t ngroups = (e.n + PPT - 1) / PPT;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = g * PPT, cnt = e.n - i0;
+    if (cnt >= PPT)
+      fused_group<PPT, TAU, ACC>(e, kc, tk, tg, i0, nsteps);
+    else
+      fused_tail<TAU, ACC>(e, kc, tk, tg, i0, (int)cnt, nsteps);
+  }
+}
+
+// Persistent grid over groups of PPT particles; each block builds the three
+// amplitude-scaled sin/cos tables (96 KB of dynamic shared memory) once.  TAU: tau per
+// particle from e.tau_src; ACC: store the last stage acceleration (one kernel per
+// combination, so the plain one is not sized for the others' registers).
+template <int PPT, int BLOCK, int MINB, bool TAU, bool ACC>
+__global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused(EnsArgs e, FlowK f, TurnsK tk, int nsteps) {
+  extern __shared__ float4 s_tab3[];
+  load_scaled_trig_tables(s_tab3, ff_from2(e.Af), ff_from2(e.Bf), ff_from2(e.Cf));
+  const StepC kc = make_stepc(e, f);
+  const TrigScaled tg{s_tab3};
+  fused_loop<PPT, TAU, ACC>(e, kc, tk, tg, nsteps);
+}
+
+}  // namespace soax

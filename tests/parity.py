@@ -71,3 +71,52 @@ def assert_parity(gpos, gvel, opos, ovel, x0, v0, taus, A, B, C, dt, steps, max_
     for i in bad:
         audit_particle([x0[c][i] for c in range(3)], [v0[c][i] for c in range(3)], A, B, C, float(taus[i]), dt, steps)
     return bad.size
+
+
+def gpu_fused_steps(x3, v3, A, B, C, tau, dt, steps):
+    """One particle advanced `steps` steps in one soax_step_fused launch."""
+    p = sx.Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], 1, shadow=False)
+    p.load({"pos": [np.array([x]) for x in x3], "vel": [np.array([v], np.float32) for v in v3]})
+    p.step_fused(sx.Flow(A=A, B=B, C=C, tau=tau, dt=dt), steps)
+    d = p.numpy()
+    return np.array([a[0] for a in d["pos"]]), np.array([a[0] for a in d["vel"]], np.float32)
+
+
+def audit_particle_fused(x0, v0, A, B, C, tau, dt, steps):
+    """Audit of a particle that soax_step_fused left out of tolerance.  The fused kernel
+    keeps its position between steps in fixed point, so it is replayed on its own
+    trajectory: the first s steps of a fused launch are the state a launch of s steps
+    returns.  Up to the first step whose f32 velocity differs from the oracle's, positions
+    must agree within 1e-13 per step; at that step the velocities must be one f32 ulp
+    apart with the oracle's f64 value within 1e-14 (relative) of the midpoint between
+    them.  Later steps follow from that flip.  A particle out of tolerance with no such
+    flip fails."""
+    x = np.array(x0, np.float64)
+    v = np.array(v0, np.float32)
+    for s in range(1, steps + 1):
+        ox, ovn, _ = oracle.step_one_detail(A, B, C, tau, dt, x, v)
+        ov = ovn.astype(np.float32)
+        gx, gv = gpu_fused_steps(x0, v0, A, B, C, tau, dt, s)
+        dx = np.abs(gx - ox)
+        dx = np.minimum(dx, sx.TWO_PI - dx)
+        assert np.all(dx <= 1e-13 * s), f"step {s}: position differs by {dx.max()}"
+        if not np.array_equal(gv, ov):
+            for c in range(3):
+                if gv[c] != ov[c]:
+                    gap = abs(np.nextafter(ov[c], gv[c], dtype=np.float32) - gv[c])
+                    assert gap == 0, f"step {s}: velocity differs by more than one f32 ulp"
+                    mid = (np.float64(gv[c]) + np.float64(ov[c])) / 2
+                    assert abs(ovn[c] - mid) <= 1e-14 * abs(ovn[c]), f"step {s}: flip away from an f32 midpoint"
+            return 1
+        x, v = ox, ov
+    raise AssertionError("out of tolerance without a velocity flip")
+
+
+def assert_parity_fused(gpos, gvel, opos, ovel, x0, v0, taus, A, B, C, dt, steps, max_audit=20):
+    """assert_parity for soax_step_fused results (audit_particle_fused)."""
+    bad = np.flatnonzero(out_of_tolerance(gpos, gvel, opos, ovel))
+    assert bad.size <= max_audit, f"{bad.size} particles out of tolerance"
+    for i in bad:
+        audit_particle_fused([x0[c][i] for c in range(3)], [v0[c][i] for c in range(3)], A, B, C, float(taus[i]),
+                             dt, steps)
+    return bad.size

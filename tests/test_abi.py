@@ -89,6 +89,13 @@ def test_bind_validation_and_step_validation_without_gpu():
     assert L.soax_step(h, C.byref(fl), -1, None) == -1
     assert b"nsteps" in L.soax_last_error()
     assert L.soax_step(None, C.byref(fl), 1, None) == -1
+    # The fused step validates the same way, before any launch.
+    assert L.soax_step_fused(h, C.byref(fl), 1, None) == -8
+    assert L.soax_step_fused(h, C.byref(bad), 1, None) == -2
+    assert L.soax_step_fused(h, C.byref(neg), 1, None) == -1
+    assert L.soax_step_fused(h, C.byref(fl), -1, None) == -1
+    assert b"nsteps" in L.soax_last_error()
+    assert L.soax_step_fused(None, C.byref(fl), 1, None) == -1
     L.soax_destroy(h)
 
 
@@ -97,6 +104,7 @@ def test_empty_handle_is_a_no_op():
     rc, h = _create(sx.BASIC_SCHEMA, 0)
     fl = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 1, 2, -1)
     assert L.soax_step(h, C.byref(fl), 3, None) == 0
+    assert L.soax_step_fused(h, C.byref(fl), 3, None) == 0
     assert L.soax_soa_to_aos(h, None, None) == 0
     L.soax_destroy(h)
 

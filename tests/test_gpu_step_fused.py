@@ -1,0 +1,176 @@
+"""GPU parity of soax_step_fused (all steps of a call in one pass over the planes, the
+position carried between steps as 64-bit fixed-point turns) against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1710_03462_b300 as sx
+import soax_inputs
+from parity import assert_parity_fused
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_both(n, steps, A=1.0, B=1.0, C=1.0, tau=0.1, dt=1e-3, seed=0):
+    d = soax_inputs.basic_set(n, seed)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    p.load(d)
+    p.step_fused(sx.Flow(A=A, B=B, C=C, tau=tau, dt=dt), steps)
+    g = p.numpy()
+    opos = [a.copy() for a in d["pos"]]
+    ovel = [a.copy() for a in d["vel"]]
+    oracle.step_soa(opos, ovel, A, B, C, tau, dt, steps)
+    return d, g, opos, ovel
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 1023, 65537])
+def test_fused_small_and_ragged(n):
+    d, g, opos, ovel = _run_both(n, 20, seed=n)
+    assert_parity_fused(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], np.full(n, 0.1), 1.0, 1.0, 1.0, 1e-3, 20)
+    assert np.array_equal(g["id"][0], d["id"][0])
+    for c in range(3):
+        assert np.all((g["pos"][c] >= 0.0) & (g["pos"][c] < sx.TWO_PI))
+
+
+def test_fused_plain_n65536_100_steps_one_launch():
+    """The 65,536-particle workload: all 100 steps in a single launch."""
+    w = soax_inputs.WORKLOADS["plain_n65536"]
+    d, g, opos, ovel = _run_both(w["n"], w["steps"], w["A"], w["B"], w["C"], w["tau"], w["dt"], w["seed"])
+    nbad = assert_parity_fused(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], np.full(w["n"], w["tau"]),
+                               w["A"], w["B"], w["C"], w["dt"], w["steps"])
+    assert nbad <= 5
+
+
+def test_fused_agrees_with_per_step_launches():
+    """soax_step_fused(10) against ten soax_step launches: velocities equal except for
+    rare f32 midpoint flips, positions within a few ulps per step."""
+    n, steps = 100003, 10
+    d = soax_inputs.basic_set(n, 11)
+    f = sx.Flow(tau=0.1, dt=1e-3)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    p.load(d)
+    p.step_fused(f, steps)
+    q = sx.Particles(sx.BASIC_SCHEMA, n)
+    q.load(d)
+    q.step(f, steps)
+    a, b = p.numpy(), q.numpy()
+    diff_v = np.zeros(n, bool)
+    for c in range(3):
+        diff_v |= a["vel"][c] != b["vel"][c]
+    assert diff_v.sum() <= 2
+    ok = ~diff_v
+    for c in range(3):
+        dx = np.abs(a["pos"][c] - b["pos"][c])
+        dx = np.minimum(dx, sx.TWO_PI - dx)
+        assert dx[ok].max() <= 1e-14
+
+
+def test_fused_ragged_tail_bit_equal_to_full_group():
+    """A particle handled by the scalar tail (odd n) gets the same bits as in a full
+    vector group (even n)."""
+    n = 4097
+    d = soax_inputs.basic_set(n + 1, 5)
+    f = sx.Flow(tau=0.3, dt=2e-3)
+    outs = []
+    for m in (n, n + 1):
+        p = sx.Particles(sx.BASIC_SCHEMA, m)
+        p.load({k: [a[:m] for a in v] for k, v in d.items()})
+        p.step_fused(f, 9)
+        outs.append(p.numpy())
+    for k in ("pos", "vel"):
+        for x, y in zip(outs[0][k], outs[1][k]):
+            assert x.tobytes() == y[:n].tobytes()
+
+
+def test_fused_zero_steps_and_empty():
+    p = sx.Particles(sx.BASIC_SCHEMA, 0)
+    p.step_fused(sx.Flow(), 5)
+    d = soax_inputs.basic_set(100)
+    q = sx.Particles(sx.BASIC_SCHEMA, 100)
+    q.load(d)
+    q.step_fused(sx.Flow(), 0)
+    assert all(np.array_equal(a, b) for a, b in zip(q.numpy()["pos"], d["pos"]))
+
+
+def test_fused_positions_at_the_box_edges():
+    """Positions at 0, just below 2pi and at the binary64 2pi - ulp stay in [0, 2pi) and
+    follow the oracle across the periodic boundary."""
+    edge = np.array([0.0, 5e-324, 1e-300, 2 ** -9, np.nextafter(sx.TWO_PI, 0), sx.TWO_PI - 1e-12, 3.0, 1e-7])
+    n = edge.size ** 2
+    px = np.repeat(edge, edge.size)
+    py = np.tile(edge, edge.size)
+    pz = np.roll(px, 3)
+    rng = np.random.default_rng(3)
+    vel = [rng.choice([-0.5, 0.5, 0.0, -1e-3], n).astype(np.float32) for _ in range(3)]
+    d = {"id": [np.arange(n, dtype=np.int32)], "pos": [px, py, pz], "vel": vel}
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    p.load(d)
+    p.step_fused(sx.Flow(tau=0.1, dt=1e-3), 7)
+    g = p.numpy()
+    opos = [a.copy() for a in d["pos"]]
+    ovel = [a.copy() for a in d["vel"]]
+    oracle.step_soa(opos, ovel, 1.0, 1.0, 1.0, 0.1, 1e-3, 7)
+    for c in range(3):
+        assert np.all((g["pos"][c] >= 0.0) & (g["pos"][c] < sx.TWO_PI))
+    assert_parity_fused(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], np.full(n, 0.1), 1.0, 1.0, 1.0, 1e-3, 7)
+
+
+def test_fused_wide_record_mass_tau_and_acc():
+    n, steps = 30001, 12
+    d = soax_inputs.wide_set(n, 4)
+    p = sx.Particles(sx.WIDE_SCHEMA, n)
+    p.load(d)
+    p.step_fused(sx.Flow(dt=5e-4, tau_field="mass", tau_scale=0.1, acc="acc"), steps)
+    g = p.numpy()
+    opos = [a.copy() for a in d["pos"]]
+    ovel = [a.copy() for a in d["vel"]]
+    oacc = [a.copy() for a in d["acc"]]
+    oracle.step_soa(opos, ovel, 1.0, 1.0, 1.0, 0.0, 5e-4, steps, acc=oacc, mass=d["mass"][0], tau_scale=0.1)
+    taus = 0.1 * d["mass"][0].astype(np.float64)
+    assert_parity_fused(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], taus, 1.0, 1.0, 1.0, 5e-4, steps)
+    for c in range(3):
+        assert np.allclose(g["acc"][c], oacc[c], rtol=1e-5, atol=1e-6)
+    for k in ("id", "mass", "tag"):
+        assert np.array_equal(g[k][0], d[k][0])
+
+
+@pytest.mark.parametrize("A,B,C,tau,dt", [(1.5, 0.5, 1.3, 0.01, 1e-3), (0.7, 1.4, 0.9, 0.05, 1e-3),
+                                          (1.2, 1.1, 0.6, 0.2, 5e-4)])
+def test_fused_amplitudes_and_stiff_tau(A, B, C, tau, dt):
+    n, steps = 20001, 100
+    d, g, opos, ovel = _run_both(n, steps, A, B, C, tau, dt, seed=int(tau * 1000))
+    assert_parity_fused(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], np.full(n, tau), A, B, C, dt, steps)
+
+
+@pytest.mark.parametrize("A,B,C,tau,dt,steps", [(1.3, 0.8, 1.1, 0.2, 0.02, 30), (1.0, 1.0, 1.0, 5.0, 0.5, 8),
+                                                (1.0, 1.0, 1.0, 0.3, 0.3, 6)])
+def test_fused_long_shifts(A, B, C, tau, dt, steps):
+    """Half-step shifts beyond the shift series (the midpoint from the table, in turns)
+    and, at dt >= 0.3, displacements dt vm beyond the fast fixed-point conversion."""
+    n = 20001
+    d, g, opos, ovel = _run_both(n, steps, A, B, C, tau, dt, seed=77)
+    assert_parity_fused(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], np.full(n, tau), A, B, C, dt, steps)
+
+
+def test_fused_full_size_sorted_n16M_sampled():
+    """The 16.7M-particle workload in the launch the bench times (10 steps in one pass),
+    checked on every 4096th particle against the oracle."""
+    w = soax_inputs.WORKLOADS["sorted_n16M"]
+    n, steps = w["n"], w["sort_every"]
+    d = soax_inputs.basic_set(n, w["seed"])
+    p = sx.Particles(sx.BASIC_SCHEMA, n, shadow=False)
+    p.load(d)
+    p.step_fused(sx.Flow(A=w["A"], B=w["B"], C=w["C"], tau=w["tau"], dt=w["dt"]), steps)
+    idx = np.arange(0, n, 4096)
+    gpos = [t[idx].cpu().numpy() for t in p.field("pos")]
+    gvel = [t[idx].cpu().numpy() for t in p.field("vel")]
+    x0 = [np.ascontiguousarray(a[idx]) for a in d["pos"]]
+    v0 = [np.ascontiguousarray(a[idx]) for a in d["vel"]]
+    opos = [a.copy() for a in x0]
+    ovel = [a.copy() for a in v0]
+    oracle.step_soa(opos, ovel, w["A"], w["B"], w["C"], w["tau"], w["dt"], steps)
+    assert_parity_fused(gpos, gvel, opos, ovel, x0, v0, np.full(idx.size, w["tau"]), w["A"], w["B"], w["C"], w["dt"],
+                        steps)
+    del p
+    torch.cuda.empty_cache()
