@@ -454,12 +454,17 @@ def secondary_rows(sx, torch, p, d, dev):
         flows.append(sx.Flow(A=abc[e, 0], B=abc[e, 1], C=abc[e, 2], tau=float(tau), dt=wb["dt"]))
     total = int(sizes.sum())
     nst = 5
+    # One persistent launch per step (autotuned), over nst steps.
     tune = sx.autotune(parts, flows, nsteps_probe=1)
     wsb = sx.step_batched(parts, flows, 1, tune)
     t_b = _time(torch, lambda: sx.step_batched(parts, flows, nst, tune, ws=wsb))
-    tf = sx.Tune(tune.parts_per_thread, tune.block, tune.vec_bits, 1)
-    sx.step_batched(parts, flows, 1, tf, ws=wsb)
-    t_f = _time(torch, lambda: sx.step_batched(parts, flows, nst, tf, ws=wsb))
+    # The workload's form: all its steps in ONE fused persistent launch (autotuned).
+    tf = sx.autotune(parts, flows, nsteps_probe=10, fuse=True)
+    wsf = sx.batched_workspace(parts)
+    sx.step_batched(parts, flows, 1, tf, ws=wsf)
+    kf = wb["steps"]
+    t_f = _time(torch, lambda: sx.step_batched(parts, flows, kf, tf, ws=wsf))
+    # Baseline: 512 separate plain launches per step, captured in one CUDA graph.
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
     g = torch.cuda.CUDAGraph()
@@ -469,12 +474,14 @@ def secondary_rows(sx, torch, p, d, dev):
                 q.step(f, 1, stream=s)
     torch.cuda.current_stream(dev).wait_stream(s)
     t_plain_b = _time(torch, lambda: [g.replay() for _ in range(nst)])
-    rows["batched"] = {"ensembles": len(parts), "particles": total, "steps": nst,
-                       "tune": tune.__dict__,
-                       "persistent_particle-steps/s": total * nst / t_b,
-                       "fused_particle-steps/s": total * nst / t_f,
-                       "plain_512_launches_particle-steps/s": total * nst / t_plain_b,
-                       "persistent_over_plain": t_plain_b / t_b}
+    rows["batched"] = {"ensembles": len(parts), "particles": total,
+                       "persistent": {"steps": nst, "tune": tune.__dict__,
+                                      "particle-steps/s": total * nst / t_b},
+                       "fused": {"steps": kf, "launches": 1, "tune": tf.__dict__, "ms": t_f * 1e3,
+                                 "particle-steps/s": total * kf / t_f},
+                       "plain_512_launches": {"steps": nst, "particle-steps/s": total * nst / t_plain_b},
+                       "persistent_over_plain": t_plain_b / t_b,
+                       "fused_over_plain": (t_plain_b / nst) / (t_f / kf)}
     del parts, g
     torch.cuda.empty_cache()
     return rows

@@ -83,8 +83,10 @@ typedef struct {
 } soax_flow;
 
 /* Launch shape of the batched step.  parts_per_thread: 1, 2 or 4 particles per thread;
- * block: 64..512, a multiple of 32; vec_bits: 64 or 128 (width of each plane load);
- * fuse_steps: 0 = one pass over memory per step, 1 = all nsteps in registers. */
+ * block: 64..512, a multiple of 32; vec_bits: 64 or 128 (width of each plane load; the
+ * fused form loads each plane once and ignores it); fuse_steps: 0 = one launch and one
+ * pass over memory per step (soax_step's arithmetic), 1 = all nsteps of the call in
+ * registers in one launch (soax_step_fused's arithmetic). */
 typedef struct {
   int32_t parts_per_thread;
   int32_t block;
@@ -312,15 +314,27 @@ int soax_batched_workspace_bytes(const soax_t* hs, int32_t nens, const soax_tune
 /* Advance nens (1..4096) independent ensembles (each its own handle and soax_flow; dt
  * must be equal) nsteps steps, every step one persistent launch over all ensembles (or,
  * with tune->fuse_steps, one launch for all steps).  Per particle the arithmetic is
- * bit-identical to soax_step.  The first call for a given (hs, fls, tune, ws) builds a
- * tile table on the host and copies it into ws, synchronising the stream; later calls
- * with the same arguments only launch, so they can be captured in a CUDA graph.
+ * bit-identical to soax_step (to soax_step_fused with tune->fuse_steps), whatever the
+ * launch shape.  The first call for a given (hs, fls, tune, ws) builds a tile table on
+ * the host and copies it into ws, synchronising the stream; later calls with the same
+ * arguments only launch, so they can be captured in a CUDA graph.
  * tune == NULL: parts_per_thread 4, block 256, vec_bits 128, no fusion. */
 int soax_step_batched(const soax_t* hs, const soax_flow* fls, int32_t nens, int32_t nsteps,
                       const soax_tune* tune, void* ws, size_t ws_bytes, void* stream);
 
-/* Time every candidate launch shape on nsteps_probe steps of the given ensembles (which
- * it advances: pass scratch copies) and write the fastest to out.  Synchronises. */
+/* Forget the plan soax_step_batched recorded for the workspace at ws (NULL or unknown:
+ * no effect): the next call with it uploads its plan again.  The library skips the upload
+ * when a workspace address comes back with the same plan, so call this whenever the
+ * memory behind a workspace may have been written by anything else -- in particular
+ * after allocating a workspace at an address an earlier, freed one had.  A plan the
+ * memory no longer holds is not followed: the kernels find its header changed, do
+ * nothing and record SOAX_EINVAL for soax_sync. */
+int soax_batched_forget(const void* ws);
+
+/* Time every candidate launch shape of one form on nsteps_probe steps of the given
+ * ensembles (which it advances: pass scratch copies) and write the fastest to out.  The
+ * form is read from out->fuse_steps on entry (0: one launch per step, 1: fused) and kept.
+ * Synchronises. */
 int soax_autotune(const soax_t* hs, const soax_flow* fls, int32_t nens, int32_t nsteps_probe,
                   void* ws, size_t ws_bytes, soax_tune* out, void* stream);
 

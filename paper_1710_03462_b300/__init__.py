@@ -369,15 +369,21 @@ def _flows(parts, flows):
 
 
 def batched_workspace(parts):
+    """A fresh workspace for step_batched.  Its address may be one an earlier, freed
+    workspace had, so the library is told to forget any plan it recorded there."""
     b = C.c_size_t()
     _check(lib().soax_batched_workspace_bytes(_handles(parts), len(parts), None, C.byref(b)))
-    return torch.empty(max(b.value, 16), dtype=torch.uint8, device=parts[0].device)
+    ws = torch.empty(max(b.value, 16), dtype=torch.uint8, device=parts[0].device)
+    _check(lib().soax_batched_forget(_ptr(ws)), "soax_batched_forget")
+    return ws
 
 
 def step_batched(parts, flows, nsteps, tune: Tune = None, ws=None, stream=None):
-    """Advance every ensemble nsteps steps, one persistent launch per step (or one in
-    total with tune.fuse_steps).  The first call for a new (ensembles, tune, ws) uploads a
-    tile plan and synchronises; later identical calls only launch."""
+    """Advance every ensemble nsteps steps, one persistent launch per step (bit-identical
+    to Particles.step per ensemble) or, with tune.fuse_steps, one launch in total
+    (bit-identical to Particles.step_fused per ensemble).  The first call for a new
+    (ensembles, tune, ws) uploads a tile plan and synchronises; later identical calls only
+    launch."""
     ws = batched_workspace(parts) if ws is None else ws
     t = tune.c() if tune is not None else None
     _check(lib().soax_step_batched(_handles(parts), _flows(parts, flows), len(parts), int(nsteps),
@@ -397,11 +403,13 @@ def _tune_key(parts):
     return f"{gpu}|{hashlib.sha1(schema.encode()).hexdigest()[:12]}|n2^{total.bit_length()}|e{len(parts)}"
 
 
-def autotune(parts, flows, nsteps_probe=2, use_cache=True, stream=None):
-    """Pick the fastest launch shape for step_batched on these ensembles.  Times every
-    candidate on scratch copies (the ensembles are not modified) and caches the result
-    in ~/.cache/soax_b300/autotune.json keyed by (GPU, schema, size bucket, #ensembles)."""
-    key = _tune_key(parts)
+def autotune(parts, flows, nsteps_probe=2, use_cache=True, stream=None, fuse=False):
+    """Pick the fastest launch shape for step_batched on these ensembles, for one launch
+    per step (fuse=False) or for the fused form (fuse=True: all steps of a call in one
+    launch).  Times every candidate on scratch copies (the ensembles are not modified)
+    and caches the result in ~/.cache/soax_b300/autotune.json keyed by (GPU, schema,
+    size bucket, #ensembles, form)."""
+    key = _tune_key(parts) + ("|fused" if fuse else "")
     path = _tune_cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -421,6 +429,7 @@ def autotune(parts, flows, nsteps_probe=2, use_cache=True, stream=None):
         scratch.append(q)
     ws = batched_workspace(scratch)
     out = soax_tune()
+    out.fuse_steps = 1 if fuse else 0
     _check(lib().soax_autotune(_handles(scratch), _flows(scratch, flows), len(scratch), int(nsteps_probe), _ptr(ws),
                                ws.numel(), C.byref(out), _stream(stream)), "soax_autotune")
     t = Tune(out.parts_per_thread, out.block, out.vec_bits, out.fuse_steps)

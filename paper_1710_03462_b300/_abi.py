@@ -66,6 +66,7 @@ SIGNATURES = {
     "soax_step_adjoint": [_p, _P(soax_flow), _i32, _i32, _p, _sz, _P(_p), _P(_p), _P(_p), _P(_p), _p, _p],
     "soax_minimage_loss": [_p, _i32, _P(_p), _p, _P(_p), _p, _sz, _p],
     "soax_batched_workspace_bytes": [_P(_p), _i32, _P(soax_tune), _P(_sz)],
+    "soax_batched_forget": [_p],
     "soax_step_batched": [_P(_p), _P(soax_flow), _i32, _i32, _P(soax_tune), _p, _sz, _p],
     "soax_autotune": [_P(_p), _P(soax_flow), _i32, _i32, _p, _sz, _P(soax_tune), _p],
     "soax_sync": [_p],

@@ -97,17 +97,25 @@ __device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, c
   }
 }
 
+// The particles [i0, i0 + cnt): the vector path for a full group, the scalar path for a
+// ragged one.
+template <int PPT, bool TAU, bool ACC, class Trig>
+__device__ __forceinline__ void fused_span(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const Trig& trig,
+                                           int64_t i0, int64_t cnt, int nsteps) {
+  if (cnt >= PPT)
+    fused_group<PPT, TAU, ACC>(e, kc, tk, trig, i0, nsteps);
+  else
+    fused_tail<TAU, ACC>(e, kc, tk, trig, i0, (int)cnt, nsteps);
+}
+
 template <int PPT, bool TAU, bool ACC>
 __device__ __forceinline__ void fused_loop(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const TrigScaled& tg,
                                            int nsteps) {
   const int64_t ngroups = (e.n + PPT - 1) / PPT;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i0 = g * PPT, cnt = e.n - i0;
-    if (cnt >= PPT)
-      fused_group<PPT, TAU, ACC>(e, kc, tk, tg, i0, nsteps);
-    else
-      fused_tail<TAU, ACC>(e, kc, tk, tg, i0, (int)cnt, nsteps);
+    const int64_t i0 = g * PPT;
+    fused_span<PPT, TAU, ACC>(e, kc, tk, tg, i0, e.n - i0, nsteps);
   }
 }
 

@@ -111,6 +111,7 @@ def test_empty_handle_is_a_no_op():
 
 def test_workspace_sizes():
     L = sx.lib()
+    assert L.soax_batched_forget(None) == 0  # unknown workspace: no effect
     b = C.c_size_t()
     assert L.soax_radix_workspace_bytes(1 << 24, 15, C.byref(b)) == 0
     # 2 passes: counts (512 x 4096 x 4) + totals + one ping-pong pair of n u32.
