@@ -5,10 +5,11 @@
 
 Workload (one "step" of this benchmark): the 16,777,216-particle set {i32 id, f64 pos[3],
 f32 vel[3]} in the ABC flow (A = B = C = 1, tau = 0.1, dt = 1e-3); one bench step is one
-sort interval: 10 midpoint-RK2 steps in one pass over the planes (soax_step_fused: each
-particle loaded once, advanced 10 steps in registers, stored once) followed by the cell
-sort on a 32^3 grid (keys, stable radix sort, permute-gather of every plane).  K bench
-steps = 10 K RK2 steps; the default K = 100 is the full 1000-step run.
+sort interval: 10 midpoint-RK2 steps in one pass over the planes (soax_step_fused_keys:
+each particle loaded once, advanced 10 steps in registers, stored once together with its
+cell key on the 32^3 grid) followed by the cell sort of those keys (stable radix sort,
+permute-gather of every plane: soax_sort_by_keys).  K bench steps = 10 K RK2 steps; the
+default K = 100 is the full 1000-step run.
 
 Metric: particle-steps/s (whole job, all ranks).  The dominant kernel is the fused step;
 with the planes moved once per 10 steps it is bound by instruction issue, not by HBM.  Its
@@ -259,13 +260,15 @@ def run_soax(args):
     ws = p.sort_workspace(WL["grid"])
     stream = torch.cuda.current_stream(dev)
 
+    keys = torch.empty(n, dtype=torch.int32, device=dev)
+
     def bench_step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        p.step_fused(flow, RK2_PER_STEP)
+        p.step_fused(flow, RK2_PER_STEP, grid=WL["grid"], keys=keys)
         if ev is not None:
             ev[1].record(stream)
-        p.sort_by_cell(WL["grid"], ws)
+        p.sort_by_keys(WL["grid"], keys, ws)
         if ev is not None:
             ev[2].record(stream)
 
@@ -321,7 +324,7 @@ def run_soax(args):
     rec = ncu_record("k_step_soa_fused")
     inst = float(rec["inst_per_particle_step"]) if rec and "inst_per_particle_step" in rec else None
     achieved = inst * n * RK2_PER_STEP / fused_s / 1e12 if inst else None
-    sort_launches = 1 + 3 * 2 + 1  # keys, (upsweep, scan, downsweep) x 2 passes, permute
+    sort_launches = 3 * 2 + 1  # (upsweep, scan, downsweep) x 2 passes, permute; the keys come with the step
     line = {
         "metric": METRIC, "value": tot_units / max_el, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_el / args.steps * 1e3,

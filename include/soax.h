@@ -189,6 +189,14 @@ int soax_step(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream);
  * soax_step; acc receives the last step's a2. */
 int soax_step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream);
 
+/* soax_step_fused that also writes the cell keys of the final positions (the flow's
+ * position field) on a grid^3 grid into keys (n u32, 16-byte aligned, caller-owned),
+ * bit-identical to soax_cell_keys on the result, as the particles are stored: the sort
+ * that follows (soax_sort_by_keys) needs no key pass over the positions.  grid in
+ * 1..1024.  nsteps = 0 writes the keys of the current positions. */
+int soax_step_fused_keys(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t grid, uint32_t* keys,
+                         void* stream);
+
 /* The same step, bit-identical per particle, on AoS records in place (layout from
  * soax_aos_layout; the flow's field indices refer to this handle's schema). */
 int soax_step_aos(soax_t h, void* aos_dev, const soax_flow* fl, int32_t nsteps, void* stream);
@@ -228,6 +236,14 @@ int soax_sort_workspace_bytes(soax_t h, int32_t grid, size_t* bytes);
 int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_bytes, void* stream);
 int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
                       uint32_t** perm);
+
+/* soax_sort_by_cell with its key pass done already: stable radix sort of the given keys
+ * (n u32, each < grid^3, as soax_cell_keys or soax_step_fused_keys write them; only their
+ * low bits up to grid^3 - 1 are sorted), permute-gather of all fields into the shadow
+ * set, flip.  ws as for soax_sort_by_cell (soax_sort_results gives the sorted keys and
+ * the permutation in it); keys must not overlap ws's sorted-key, permutation or radix
+ * regions. */
+int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes, void* stream);
 
 /* soax_sort_by_cell without a caller workspace.  The paper has no counterpart: this is
  * for hosts that cannot allocate device memory where they sort -- C or Fortran codes

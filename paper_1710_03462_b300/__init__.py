@@ -190,10 +190,19 @@ class Particles:
         fl = self.flow(f)
         _check(lib().soax_step(self.h, C.byref(fl), int(nsteps), _stream(stream)), "soax_step")
 
-    def step_fused(self, f: Flow, nsteps=1, stream=None):
-        """nsteps steps in one pass over the planes (soax_step_fused)."""
+    def step_fused(self, f: Flow, nsteps=1, stream=None, grid=None, keys=None):
+        """nsteps steps in one pass over the planes (soax_step_fused).  With grid (and
+        optionally keys, an int32 tensor of n elements), also the cell keys of the final
+        positions (soax_step_fused_keys); returns the keys tensor then."""
         fl = self.flow(f)
-        _check(lib().soax_step_fused(self.h, C.byref(fl), int(nsteps), _stream(stream)), "soax_step_fused")
+        if grid is None:
+            _check(lib().soax_step_fused(self.h, C.byref(fl), int(nsteps), _stream(stream)), "soax_step_fused")
+            return None
+        if keys is None:
+            keys = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.device)
+        _check(lib().soax_step_fused_keys(self.h, C.byref(fl), int(nsteps), int(grid), _ptr(keys), _stream(stream)),
+               "soax_step_fused_keys")
+        return keys
 
     def aos_layout(self):
         rb = C.c_int64()
@@ -231,6 +240,14 @@ class Particles:
         """Cell sort of every field; returns (sorted keys, perm) as int32 views into ws."""
         ws = self.sort_workspace(grid) if ws is None else ws
         _check(lib().soax_sort_by_cell(self.h, int(grid), _ptr(ws), ws.numel(), _stream(stream)), "soax_sort_by_cell")
+        return self.sort_results(grid, ws)
+
+    def sort_by_keys(self, grid, keys, ws=None, stream=None):
+        """sort_by_cell with the keys given (from step_fused(..., keys=...) or cell_keys):
+        no key pass.  Returns (sorted keys, perm) as int32 views into ws."""
+        ws = self.sort_workspace(grid) if ws is None else ws
+        _check(lib().soax_sort_by_keys(self.h, int(grid), _ptr(keys), _ptr(ws), ws.numel(), _stream(stream)),
+               "soax_sort_by_keys")
         return self.sort_results(grid, ws)
 
     def sort_results(self, grid, ws):

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "cell_key.cuh"
 #include "soax_internal.h"
 
 namespace soax {
@@ -88,53 +89,25 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
 }
 
 // ------------------------------------------------------------------ cell keys
-// floor(RN(x * c)) for 0 <= x and 0 < c with x * c < 2^31, computed exactly with integer
-// instructions (the binary64 product rounded to nearest-even, then truncated), so the
-// result equals (int)(x * c) of IEEE binary64 arithmetic without using the FP64 pipe.
-// cm: c's 53-bit significand; ce: c's biased exponent.
-__device__ __forceinline__ int floor_mul_rn(double x, uint64_t cm, int ce) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0 || (b >> 63)) return 0;  // zero, subnormal or negative: the product truncates to 0
-  const uint64_t mx = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  // M = mx * cm, 105 or 106 bits; x c = M 2^(ex + ce - 2150).
-  const uint64_t hi = __umul64hi(mx, cm), lo = mx * cm;
-  const int d = (hi >> 41) ? 53 : 52;  // bits to drop to keep 53 significant bits
-  uint64_t mr = (hi << (64 - d)) | (lo >> d);
-  const uint64_t rem = lo & ((1ull << d) - 1), half = 1ull << (d - 1);
-  if (rem > half || (rem == half && (mr & 1))) ++mr;  // round to nearest, ties to even
-  const int t = 2150 - ex - ce - d;  // RN(x c) = mr 2^-t
-  if (t >= 64) return 0;
-  if (t <= 0) return 0x7FFFFFFF;  // outside the key range (clamped by the caller)
-  return (int)(mr >> t);
-}
-
-// Cell index of one coordinate.  Fast path: P = x c 2^51 in fixed point (X = x 2^61
-// exact for 2^-8 <= x < 8, times c 2^54 rounded, high 64 bits) is within 3 units of the
-// exact product; the binary64 rounding of x c moves it by at most 2^-44 (x c < 2^10),
-// i.e. 128 units, so unless P lies within 131 units of an integer boundary its floor
-// equals floor(RN(x c)).  Otherwise (probability ~2^-42, or x < 2^-8) the exact path.
-__device__ __forceinline__ int cell_index(double x, uint64_t cfx, uint64_t cm, int ce) {
-  const uint64_t b = (uint64_t)__double_as_longlong(x);
-  const int e = (int)(b >> 52);  // sign bit included: negative x takes the exact path
-  if (e >= 1015 && e <= 1025) {
-    const uint64_t X = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (e - 1014);
-    const uint64_t P = __umul64hi(X, cfx);
-    const uint64_t frac = P & ((1ull << 51) - 1);
-    if (frac >= 131 && frac <= (1ull << 51) - 132) return (int)(P >> 51);
-  }
-  return floor_mul_rn(x, cm, ce);
-}
-
 __global__ void __launch_bounds__(256) k_cell_keys(const double* __restrict__ px, const double* __restrict__ py,
-                                                   const double* __restrict__ pz, int64_t n, uint64_t cfx,
-                                                   uint64_t cm, int ce, int G, uint32_t* __restrict__ keys) {
+                                                   const double* __restrict__ pz, int64_t n, CellKeyK ck,
+                                                   uint32_t* __restrict__ keys) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int ix = min(cell_index(px[i], cfx, cm, ce), G - 1);
-  int iy = min(cell_index(py[i], cfx, cm, ce), G - 1);
-  int iz = min(cell_index(pz[i], cfx, cm, ce), G - 1);
-  keys[i] = (uint32_t)((iz * G + iy) * G + ix);
+  keys[i] = cell_key(px[i], py[i], pz[i], ck);
+}
+
+CellKeyK make_cell_key_k(int grid) {
+  const double c = (double)grid / SOAX_TWO_PI_HOST;
+  uint64_t cb;
+  std::memcpy(&cb, &c, sizeof cb);
+  CellKeyK k;
+  k.cm = (cb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  k.ce = (int)((cb >> 52) & 0x7FF);
+  // c 2^54 rounded to an integer (c < 2^8 for G <= 1024, so it fits 62 bits).
+  k.cfx = (uint64_t)std::llround(std::ldexp(c, 54));
+  k.G = grid;
+  return k;
 }
 
 // ------------------------------------------------------------------ radix passes
@@ -390,14 +363,7 @@ extern "C" int soax_cell_keys(soax_t h, int32_t pos_field, int32_t grid, uint32_
   const double* py = (const double*)h->planes[h->current][fp + 1];
   const double* pz = (const double*)h->planes[h->current][fp + 2];
   if (!px || !py || !pz) return fail(SOAX_EUNBOUND, "soax_cell_keys: position planes not bound");
-  const double c = (double)grid / SOAX_TWO_PI_HOST;
-  uint64_t cb;
-  std::memcpy(&cb, &c, sizeof cb);
-  const uint64_t cm = (cb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int ce = (int)((cb >> 52) & 0x7FF);
-  // c 2^54 rounded to an integer (c < 2^8 for G <= 1024, so it fits 62 bits).
-  const uint64_t cfx = (uint64_t)std::llround(std::ldexp(c, 54));
-  k_cell_keys<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n, cfx, cm, ce, grid, keys);
+  k_cell_keys<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n, make_cell_key_k(grid), keys);
   return check_launch("soax_cell_keys");
 }
 
@@ -511,6 +477,34 @@ extern "C" int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_byt
   return SOAX_OK;
 }
 
+// The radix sort of the given keys and the permute-gather (soax_sort_by_cell after its
+// key pass).  keys may lie in the workspace's own key region.
+static int sort_by_keys_impl(soax_t h, int32_t grid, const uint32_t* keys, void* ws, void* stream) {
+  const SortWs w = sort_ws_plan(h->n, grid);
+  char* base = static_cast<char*>(ws);
+  uint32_t* skeys = reinterpret_cast<uint32_t*>(base + w.off_skeys);
+  uint32_t* perm = reinterpret_cast<uint32_t*>(base + w.off_perm);
+  if (int r = soax_radix_sort_pairs(keys, nullptr, skeys, perm, h->n, key_bits_for_grid(grid), base + w.off_radix,
+                                    w.rp.total, stream))
+    return r;
+  return soax_permute(h, perm, stream);
+}
+
+extern "C" int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, "soax_sort_by_keys: grid must be in 1..1024");
+  const SortWs w = sort_ws_plan(h->n, grid);
+  if (h->n == 0) return SOAX_OK;
+  if (!keys) return fail(SOAX_EINVAL, "soax_sort_by_keys: keys is NULL");
+  if (!aligned16(keys)) return fail(SOAX_EALIGN, "soax_sort_by_keys: keys not 16-byte aligned");
+  if (!ws || ws_bytes < w.total) return fail(SOAX_ENOMEM, "soax_sort_by_keys: workspace too small");
+  if (!aligned16(ws)) return fail(SOAX_EALIGN, "soax_sort_by_keys: workspace not 16-byte aligned");
+  if (int r = live_planes_bound(h, h->current)) return r;
+  if (int r = live_planes_bound(h, h->current ^ 1)) return r;
+  return sort_by_keys_impl(h, grid, keys, ws, stream);
+}
+
 extern "C" int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_bytes, void* stream) {
   if (int r = check_handle(h)) return r;
   if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, "soax_sort_by_cell: grid must be in 1..1024");
@@ -522,13 +516,7 @@ extern "C" int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_byt
   if (!aligned16(ws)) return fail(SOAX_EALIGN, "soax_sort_by_cell: workspace not 16-byte aligned");
   if (int r = live_planes_bound(h, h->current)) return r;
   if (int r = live_planes_bound(h, h->current ^ 1)) return r;
-  char* base = static_cast<char*>(ws);
-  uint32_t* keys = reinterpret_cast<uint32_t*>(base + w.off_keys);
-  uint32_t* skeys = reinterpret_cast<uint32_t*>(base + w.off_skeys);
-  uint32_t* perm = reinterpret_cast<uint32_t*>(base + w.off_perm);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + w.off_keys);
   if (int r = soax_cell_keys(h, pf, grid, keys, stream)) return r;
-  if (int r = soax_radix_sort_pairs(keys, nullptr, skeys, perm, h->n, key_bits_for_grid(grid), base + w.off_radix,
-                                    w.rp.total, stream))
-    return r;
-  return soax_permute(h, perm, stream);
+  return sort_by_keys_impl(h, grid, keys, ws, stream);
 }

@@ -1,9 +1,11 @@
 // Kernel template of soax_step_fused: each thread loads groups of PPT particles once,
 // advances them nsteps midpoint-RK2 steps in registers (positions as 64-bit fixed-point
-// turns, rk2_turns.cuh) and stores them once.
+// turns, rk2_turns.cuh) and stores them once; optionally with the cell keys of the final
+// positions (cell_key.cuh, the definition soax_cell_keys uses) written beside them.
 #pragma once
 #include <cstdint>
 
+#include "cell_key.cuh"
 #include "rk2_turns.cuh"
 #include "step_core.cuh"
 
@@ -13,7 +15,7 @@ namespace soax {
 // function as fused_group, so a particle gets the same bits on either path.
 template <bool TAU, bool ACC, class Trig>
 __device__ __forceinline__ void fused_tail(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const Trig& trig,
-                                           int64_t i0, int cnt, int nsteps) {
+                                           int64_t i0, int cnt, int nsteps, uint32_t* keys, const CellKeyK& ck) {
   for (int j = 0; j < cnt; ++j) {
     const int64_t i = i0 + j;
     uint64_t T[3] = {to_turns(e.px[i]), to_turns(e.py[i]), to_turns(e.pz[i])};
@@ -21,9 +23,11 @@ __device__ __forceinline__ void fused_tail(const EnsArgs& e, const StepC& kc, co
     StepC k = kc;
     if constexpr (TAU) set_inv_tau(k, particle_inv_tau<true>(e, i));
     for (int s = 0; s < nsteps; ++s) rk2_step_turns<ACC, false>(k, tk, trig, T, v, a);
-    e.px[i] = turns_to_x(T[0]);
-    e.py[i] = turns_to_x(T[1]);
-    e.pz[i] = turns_to_x(T[2]);
+    const double x = turns_to_x(T[0]), y = turns_to_x(T[1]), z = turns_to_x(T[2]);
+    e.px[i] = x;
+    e.py[i] = y;
+    e.pz[i] = z;
+    if (keys) keys[i] = cell_key(x, y, z, ck);
     e.vx[i] = v[0]; e.vy[i] = v[1]; e.vz[i] = v[2];
     if constexpr (ACC) { e.ax[i] = a[0]; e.ay[i] = a[1]; e.az[i] = a[2]; }
   }
@@ -34,7 +38,7 @@ __device__ __forceinline__ void fused_tail(const EnsArgs& e, const StepC& kc, co
 // series (near_shift) runs straight-line code for that step.
 template <int PPT, bool TAU, bool ACC, class Trig>
 __device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const Trig& trig,
-                                            int64_t i0, int nsteps) {
+                                            int64_t i0, int nsteps, uint32_t* keys, const CellKeyK& ck) {
   double x[PPT], y[PPT], z[PPT];
   float vx[PPT], vy[PPT], vz[PPT];
   load_f64<PPT, 128>(e.px, i0, x);
@@ -83,6 +87,10 @@ __device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, c
   store_f64<PPT, 128>(e.px, i0, x);
   store_f64<PPT, 128>(e.py, i0, y);
   store_f64<PPT, 128>(e.pz, i0, z);
+  if (keys) {
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) keys[i0 + j] = cell_key(x[j], y[j], z[j], ck);
+  }
   store_f32<PPT, 128>(e.vx, i0, vx);
   store_f32<PPT, 128>(e.vy, i0, vy);
   store_f32<PPT, 128>(e.vz, i0, vz);
@@ -101,35 +109,38 @@ __device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, c
 // ragged one.
 template <int PPT, bool TAU, bool ACC, class Trig>
 __device__ __forceinline__ void fused_span(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const Trig& trig,
-                                           int64_t i0, int64_t cnt, int nsteps) {
+                                           int64_t i0, int64_t cnt, int nsteps, uint32_t* keys = nullptr,
+                                           const CellKeyK& ck = CellKeyK{}) {
   if (cnt >= PPT)
-    fused_group<PPT, TAU, ACC>(e, kc, tk, trig, i0, nsteps);
+    fused_group<PPT, TAU, ACC>(e, kc, tk, trig, i0, nsteps, keys, ck);
   else
-    fused_tail<TAU, ACC>(e, kc, tk, trig, i0, (int)cnt, nsteps);
+    fused_tail<TAU, ACC>(e, kc, tk, trig, i0, (int)cnt, nsteps, keys, ck);
 }
 
 template <int PPT, bool TAU, bool ACC>
 __device__ __forceinline__ void fused_loop(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const TrigScaled& tg,
-                                           int nsteps) {
+                                           int nsteps, uint32_t* keys, const CellKeyK& ck) {
   const int64_t ngroups = (e.n + PPT - 1) / PPT;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
        g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i0 = g * PPT;
-    fused_span<PPT, TAU, ACC>(e, kc, tk, tg, i0, e.n - i0, nsteps);
+    fused_span<PPT, TAU, ACC>(e, kc, tk, tg, i0, e.n - i0, nsteps, keys, ck);
   }
 }
 
 // Persistent grid over groups of PPT particles; each block builds the three
 // amplitude-scaled sin/cos tables (96 KB of dynamic shared memory) once.  TAU: tau per
 // particle from e.tau_src; ACC: store the last stage acceleration (one kernel per
-// combination, so the plain one is not sized for the others' registers).
+// combination, so the plain one is not sized for the others' registers).  keys: NULL, or
+// n u32 receiving the cell keys of the final positions on the grid of ck.
 template <int PPT, int BLOCK, int MINB, bool TAU, bool ACC>
-__global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused(EnsArgs e, FlowK f, TurnsK tk, int nsteps) {
+__global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused(EnsArgs e, FlowK f, TurnsK tk, int nsteps,
+                                                                uint32_t* __restrict__ keys, CellKeyK ck) {
   extern __shared__ float4 s_tab3[];
   load_scaled_trig_tables(s_tab3, ff_from2(e.Af), ff_from2(e.Bf), ff_from2(e.Cf));
   const StepC kc = make_stepc(e, f);
   const TrigScaled tg{s_tab3};
-  fused_loop<PPT, TAU, ACC>(e, kc, tk, tg, nsteps);
+  fused_loop<PPT, TAU, ACC>(e, kc, tk, tg, nsteps, keys, ck);
 }
 
 }  // namespace soax

@@ -104,6 +104,12 @@ def test_empty_handle_is_a_no_op():
     rc, h = _create(sx.BASIC_SCHEMA, 0)
     fl = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 1, 2, -1)
     assert L.soax_step(h, C.byref(fl), 3, None) == 0
+    # The keyed fused step and the keyed sort check the grid before anything else.
+    assert L.soax_step_fused_keys(h, C.byref(fl), 1, 0, None, None) == -1
+    assert L.soax_step_fused_keys(h, C.byref(fl), 1, 2000, None, None) == -1
+    assert L.soax_step_fused_keys(h, C.byref(fl), 1, 32, None, None) == 0
+    assert L.soax_sort_by_keys(h, 0, None, None, 0, None) == -1
+    assert L.soax_sort_by_keys(h, 32, None, None, 0, None) == 0
     assert L.soax_step_fused(h, C.byref(fl), 3, None) == 0
     assert L.soax_soa_to_aos(h, None, None) == 0
     L.soax_destroy(h)

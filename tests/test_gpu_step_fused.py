@@ -174,3 +174,49 @@ def test_fused_full_size_sorted_n16M_sampled():
                         steps)
     del p
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("schema,grid,n", [("basic", 32, 100003), ("wide", 64, 30001), ("basic", 7, 4097)])
+def test_fused_keys_equal_cell_keys(schema, grid, n):
+    """The keys the fused step writes beside the final positions are soax_cell_keys of
+    those positions, bit for bit, and the oracle's keys."""
+    if schema == "basic":
+        d, sch, f = soax_inputs.basic_set(n, 21), sx.BASIC_SCHEMA, sx.Flow(tau=0.1, dt=1e-3)
+    else:
+        d, sch = soax_inputs.wide_set(n, 22), sx.WIDE_SCHEMA
+        f = sx.Flow(dt=5e-4, tau_field="mass", tau_scale=0.1, acc="acc")
+    p = sx.Particles(sch, n)
+    p.load(d)
+    keys = p.step_fused(f, 10, grid=grid)
+    again = p.cell_keys(grid)
+    assert torch.equal(keys[:n], again)
+    g = p.numpy()
+    assert np.array_equal(keys[:n].cpu().numpy().view(np.uint32), oracle.cell_keys(*g["pos"], grid))
+    # nsteps = 0: the keys of the current positions.
+    k0 = p.step_fused(f, 0, grid=grid)
+    assert torch.equal(k0[:n], again)
+
+
+def test_sort_by_keys_equals_sort_by_cell():
+    """step_fused with keys + sort_by_keys (the bench step) gives the same planes and
+    permutation as step_fused + sort_by_cell."""
+    n, grid = 200003, 32
+    d = soax_inputs.basic_set(n, 23)
+    f = sx.Flow(tau=0.1, dt=1e-3)
+    a = sx.Particles(sx.BASIC_SCHEMA, n)
+    b = sx.Particles(sx.BASIC_SCHEMA, n)
+    a.load(d)
+    b.load(d)
+    wa, wb = a.sort_workspace(grid), b.sort_workspace(grid)
+    for _ in range(3):
+        a.step_fused(f, 10)
+        ka, pa = a.sort_by_cell(grid, wa)
+        keys = b.step_fused(f, 10, grid=grid)
+        kb, pb = b.sort_by_keys(grid, keys, wb)
+        assert torch.equal(ka, kb) and torch.equal(pa, pb)
+    ga, gb = a.numpy(), b.numpy()
+    for k in ga:
+        for x, y in zip(ga[k], gb[k]):
+            assert x.tobytes() == y.tobytes()
+    sk = ka.cpu().numpy().view(np.uint32)
+    assert np.all(np.diff(sk.astype(np.int64)) >= 0)
