@@ -5,11 +5,14 @@
 
 Workload (one "step" of this benchmark): the 16,777,216-particle set {i32 id, f64 pos[3],
 f32 vel[3]} in the ABC flow (A = B = C = 1, tau = 0.1, dt = 1e-3); one bench step is one
-sort interval: 10 midpoint-RK2 steps in one pass over the planes (soax_step_fused_keys:
-each particle loaded once, advanced 10 steps in registers, stored once together with its
-cell key on the 32^3 grid) followed by the cell sort of those keys (stable radix sort,
-permute-gather of every plane: soax_sort_by_keys).  K bench steps = 10 K RK2 steps; the
-default K = 100 is the full 1000-step run.
+sort interval: 10 midpoint-RK2 steps and a cell sort on the 32^3 grid.  The steps run in
+one pass over the planes (soax_permute_step_fused: each particle gathered once through
+the permutation the previous sort computed, advanced 10 steps in registers, stored in
+sorted order with its new cell key), then the stable radix sort of the keys gives the
+next permutation (soax_sort_perm); so every bench step does the steps, the keys, the
+radix sort and the permute-gather of every plane, with the gather riding on the next
+step's pass.  K bench steps = 10 K RK2 steps; the default K = 100 is the full 1000-step
+run.
 
 Metric: particle-steps/s (whole job, all ranks).  The dominant kernel is the fused step;
 with the planes moved once per 10 steps it is bound by instruction issue, not by HBM.  Its
@@ -57,6 +60,11 @@ L2_BYTES = 126 * 2 ** 20
 # 148 SMs, 32 lanes, at the 2032 MHz maximum SM clock (thread-instructions per second).
 SMSP_PER_SM = 4
 MAX_SM_MHZ = 2032.0
+# The bench step's dominant kernel: 10 steps with the previous sort's permute-gather and
+# the new cell keys in one pass.  Its algorithmic bytes per particle per launch: perm 4,
+# gathered record 40 (id, pos, vel), written record 40, key 4.
+STEP_KERNEL = "k_step_soa_fused_gather"
+STEP_LAUNCH_BYTES = 88
 
 
 def parse_args(argv=None):
@@ -261,14 +269,15 @@ def run_soax(args):
     stream = torch.cuda.current_stream(dev)
 
     keys = torch.empty(n, dtype=torch.int32, device=dev)
+    pending = {"perm": None}  # the permutation the last sort left, gathered by the next step
 
     def bench_step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        p.step_fused(flow, RK2_PER_STEP, grid=WL["grid"], keys=keys)
+        p.step_fused(flow, RK2_PER_STEP, grid=WL["grid"], keys=keys, perm=pending["perm"])
         if ev is not None:
             ev[1].record(stream)
-        p.sort_by_keys(WL["grid"], keys, ws)
+        pending["perm"] = p.sort_perm(WL["grid"], keys, ws)[1]
         if ev is not None:
             ev[2].record(stream)
 
@@ -321,10 +330,10 @@ def run_soax(args):
     fused_s = statistics.mean(fused_ms) / 1e3
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_inst = sms * SMSP_PER_SM * 32 * MAX_SM_MHZ * 1e6 / 1e12  # T thread-instructions/s
-    rec = ncu_record("k_step_soa_fused")
+    rec = ncu_record(STEP_KERNEL)
     inst = float(rec["inst_per_particle_step"]) if rec and "inst_per_particle_step" in rec else None
     achieved = inst * n * RK2_PER_STEP / fused_s / 1e12 if inst else None
-    sort_launches = 3 * 2 + 1  # (upsweep, scan, downsweep) x 2 passes, permute; the keys come with the step
+    sort_launches = 3 * 2  # (upsweep, scan, downsweep) x 2 passes; keys and permute-gather ride on the step
     line = {
         "metric": METRIC, "value": tot_units / max_el, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_el / args.steps * 1e3,
@@ -333,13 +342,13 @@ def run_soax(args):
                    "rk2_steps_per_step": RK2_PER_STEP, "grid": WL["grid"], "flow": "ABC A=B=C=1 tau=0.1 dt=1e-3",
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 ({n * 40 / 2**20:.0f} MiB of planes > 126 MiB)"},
-        "roofline": {"bound": "alu", "kernel": "k_step_soa_fused", "achieved": achieved, "peak": peak_inst,
+        "roofline": {"bound": "alu", "kernel": STEP_KERNEL, "achieved": achieved, "peak": peak_inst,
                      "unit": "Tinst/s", "frac": achieved / peak_inst if achieved else None,
                      "peak_kind": f"issue rate: 1 warp-instruction/clock per SM sub-partition x {SMSP_PER_SM} x "
                                   f"{sms} SMs x 32 lanes at {MAX_SM_MHZ:.0f} MHz",
                      "work_per_unit": inst, "work_unit": "thread-instructions per particle-step (ncu counter)",
-                     "units_per_launch": n * RK2_PER_STEP, "traffic": ncu_traffic("k_step_soa_fused"),
-                     "hbm_GB/s": BYTES_PER_PARTICLE_STEP * n / fused_s / 1e9,
+                     "units_per_launch": n * RK2_PER_STEP, "traffic": ncu_traffic(STEP_KERNEL),
+                     "hbm_GB/s": STEP_LAUNCH_BYTES * n / fused_s / 1e9,
                      "launch_ms": statistics.mean(fused_ms)},
         "sort_ms": statistics.mean(sort_ms),
         "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,

@@ -197,6 +197,18 @@ int soax_step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream)
 int soax_step_fused_keys(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t grid, uint32_t* keys,
                          void* stream);
 
+/* soax_permute(h, perm) followed by soax_step_fused_keys(h, fl, nsteps, grid, keys) in
+ * ONE pass: particle i of the other buffer set becomes particle perm[i] of the live set,
+ * its position and velocity advanced nsteps steps on the way and its other fields copied;
+ * then the live set flips.  Same bits as the two calls.  perm: n u32 (a permutation of
+ * 0..n-1, 16-byte aligned; an entry >= n is not read, particle 0 is used instead and
+ * SOAX_EINVAL is recorded for soax_sync), e.g. the permutation soax_sort_perm left in a
+ * sort workspace, so that a cell sort's gather costs no pass of its own.  grid = 0: no
+ * keys (keys ignored); else keys as for soax_step_fused_keys.  Both buffer sets must be
+ * bound. */
+int soax_permute_step_fused(soax_t h, const uint32_t* perm, const soax_flow* fl, int32_t nsteps, int32_t grid,
+                            uint32_t* keys, void* stream);
+
 /* The same step, bit-identical per particle, on AoS records in place (layout from
  * soax_aos_layout; the flow's field indices refer to this handle's schema). */
 int soax_step_aos(soax_t h, void* aos_dev, const soax_flow* fl, int32_t nsteps, void* stream);
@@ -244,6 +256,11 @@ int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_
  * the permutation in it); keys must not overlap ws's sorted-key, permutation or radix
  * regions. */
 int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes, void* stream);
+
+/* soax_sort_by_keys without the permute-gather: the stable permutation that sorts keys
+ * (and the sorted keys) are left in ws (soax_sort_results gives their addresses); no
+ * particle moves.  Pair it with soax_permute_step_fused, or soax_permute. */
+int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes, void* stream);
 
 /* soax_sort_by_cell without a caller workspace.  The paper has no counterpart: this is
  * for hosts that cannot allocate device memory where they sort -- C or Fortran codes

@@ -190,11 +190,20 @@ class Particles:
         fl = self.flow(f)
         _check(lib().soax_step(self.h, C.byref(fl), int(nsteps), _stream(stream)), "soax_step")
 
-    def step_fused(self, f: Flow, nsteps=1, stream=None, grid=None, keys=None):
+    def step_fused(self, f: Flow, nsteps=1, stream=None, grid=None, keys=None, perm=None):
         """nsteps steps in one pass over the planes (soax_step_fused).  With grid (and
         optionally keys, an int32 tensor of n elements), also the cell keys of the final
-        positions (soax_step_fused_keys); returns the keys tensor then."""
+        positions (soax_step_fused_keys); returns the keys tensor then.  With perm (int32
+        tensor of n elements, e.g. from sort_perm), the permute-gather of every plane by
+        perm in the same pass, into the other buffer set (soax_permute_step_fused)."""
         fl = self.flow(f)
+        if perm is not None:
+            if grid is not None and keys is None:
+                keys = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.device)
+            _check(lib().soax_permute_step_fused(self.h, _ptr(perm), C.byref(fl), int(nsteps),
+                                                 int(grid) if grid is not None else 0, _ptr(keys), _stream(stream)),
+                   "soax_permute_step_fused")
+            return keys
         if grid is None:
             _check(lib().soax_step_fused(self.h, C.byref(fl), int(nsteps), _stream(stream)), "soax_step_fused")
             return None
@@ -248,6 +257,14 @@ class Particles:
         ws = self.sort_workspace(grid) if ws is None else ws
         _check(lib().soax_sort_by_keys(self.h, int(grid), _ptr(keys), _ptr(ws), ws.numel(), _stream(stream)),
                "soax_sort_by_keys")
+        return self.sort_results(grid, ws)
+
+    def sort_perm(self, grid, keys, ws=None, stream=None):
+        """The stable permutation sorting keys, left in ws (no particle moves); returns
+        (sorted keys, perm) as int32 views into ws."""
+        ws = self.sort_workspace(grid) if ws is None else ws
+        _check(lib().soax_sort_perm(self.h, int(grid), _ptr(keys), _ptr(ws), ws.numel(), _stream(stream)),
+               "soax_sort_perm")
         return self.sort_results(grid, ws)
 
     def sort_results(self, grid, ws):

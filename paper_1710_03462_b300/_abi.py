@@ -49,6 +49,7 @@ SIGNATURES = {
     "soax_step": [_p, _P(soax_flow), _i32, _p],
     "soax_step_fused": [_p, _P(soax_flow), _i32, _p],
     "soax_step_fused_keys": [_p, _P(soax_flow), _i32, _i32, _p, _p],
+    "soax_permute_step_fused": [_p, _p, _P(soax_flow), _i32, _i32, _p, _p],
     "soax_step_aos": [_p, _p, _P(soax_flow), _i32, _p],
     "soax_cell_keys": [_p, _i32, _i32, _p, _p],
     "soax_radix_workspace_bytes": [_i64, _i32, _P(_sz)],
@@ -56,6 +57,7 @@ SIGNATURES = {
     "soax_permute": [_p, _p, _p],
     "soax_sort_workspace_bytes": [_p, _i32, _P(_sz)],
     "soax_sort_by_keys": [_p, _i32, _p, _p, _sz, _p],
+    "soax_sort_perm": [_p, _i32, _p, _p, _sz, _p],
     "soax_sort_by_cell": [_p, _i32, _p, _sz, _p],
     "soax_sort_results": [_p, _i32, _p, _sz, _P(_p), _P(_p)],
     "soax_sort_by_cell_noalloc": [_p, _i32, _p, _p],

@@ -490,6 +490,22 @@ static int sort_by_keys_impl(soax_t h, int32_t grid, const uint32_t* keys, void*
   return soax_permute(h, perm, stream);
 }
 
+extern "C" int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (int r = check_handle(h)) return r;
+  if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, "soax_sort_perm: grid must be in 1..1024");
+  const SortWs w = sort_ws_plan(h->n, grid);
+  if (h->n == 0) return SOAX_OK;
+  if (!keys) return fail(SOAX_EINVAL, "soax_sort_perm: keys is NULL");
+  if (!aligned16(keys)) return fail(SOAX_EALIGN, "soax_sort_perm: keys not 16-byte aligned");
+  if (!ws || ws_bytes < w.total) return fail(SOAX_ENOMEM, "soax_sort_perm: workspace too small");
+  if (!aligned16(ws)) return fail(SOAX_EALIGN, "soax_sort_perm: workspace not 16-byte aligned");
+  char* base = static_cast<char*>(ws);
+  return soax_radix_sort_pairs(keys, nullptr, reinterpret_cast<uint32_t*>(base + w.off_skeys),
+                               reinterpret_cast<uint32_t*>(base + w.off_perm), h->n, key_bits_for_grid(grid),
+                               base + w.off_radix, w.rp.total, stream);
+}
+
 extern "C" int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes,
                                  void* stream) {
   if (int r = check_handle(h)) return r;

@@ -80,7 +80,95 @@ static int step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t gri
   return check_launch(who);
 }
 
+using GatherKernel = void (*)(EnsArgs, EnsArgs, GatherArgs, FlowK, TurnsK, int, uint32_t*, CellKeyK);
+
+static GatherKernel gather_kernel(bool tau, bool acc) {
+  if (tau)
+    return acc ? k_step_soa_fused_gather<kFusedBlock, kFusedMinBlocks, true, true>
+               : k_step_soa_fused_gather<kFusedBlock, kFusedMinBlocks, true, false>;
+  return acc ? k_step_soa_fused_gather<kFusedBlock, kFusedMinBlocks, false, true>
+             : k_step_soa_fused_gather<kFusedBlock, kFusedMinBlocks, false, false>;
+}
+
+static int prepare_gather_kernels() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return cuda_fail(cudaGetLastError(), "soax_permute_step_fused: device");
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return SOAX_OK;
+  for (int v = 0; v < 4; ++v) {
+    const void* fn = (const void*)gather_kernel(v & 1, v & 2);
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kScaledTrigBytes);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return cuda_fail(err, "soax_permute_step_fused: kernel attributes");
+  }
+  done[dev] = true;
+  return SOAX_OK;
+}
+
+static int permute_step_fused(soax_t h, const uint32_t* perm, const soax_flow* fl, int32_t nsteps, int32_t grid,
+                              uint32_t* keys, void* stream) {
+  const char* who = "soax_permute_step_fused";
+  if (int r = check_handle(h)) return r;
+  if (nsteps < 0) return fail(SOAX_EINVAL, std::string(who) + ": nsteps < 0");
+  const int src = h->current, dst = src ^ 1;
+  EnsArgs ein, eout;
+  FlowK f;
+  if (int r = make_ens_args(h, fl, src, &ein, &f, who)) return r;
+  if (int r = make_ens_args(h, fl, dst, &eout, &f, who)) return r;
+  CellKeyK ck{};
+  if (grid) {
+    if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, std::string(who) + ": grid must be in 1..1024");
+    if (h->n > 0 && !keys) return fail(SOAX_EINVAL, std::string(who) + ": keys is NULL");
+    if (!aligned16(keys)) return fail(SOAX_EALIGN, std::string(who) + ": keys not 16-byte aligned");
+    ck = make_cell_key_k(grid);
+  }
+  if (h->n == 0) {
+    h->current = dst;
+    return SOAX_OK;
+  }
+  if (!perm) return fail(SOAX_EINVAL, std::string(who) + ": perm is NULL");
+  if (!aligned16(perm)) return fail(SOAX_EALIGN, std::string(who) + ": perm not 16-byte aligned");
+  if (int r = live_planes_bound(h, src)) return r;
+  if (int r = live_planes_bound(h, dst)) return r;
+  if (nsteps == 0) {  // the permute alone, then the keys of the permuted positions
+    if (int r = soax_permute(h, perm, stream)) return r;
+    return grid ? soax_cell_keys(h, fl->pos_field, grid, keys, stream) : SOAX_OK;
+  }
+  GatherArgs g;
+  g.perm = perm;
+  g.status = status_word();
+  if (!g.status) return fail(SOAX_ECUDA, std::string(who) + ": status word");
+  g.nother = 0;
+  for (int fi = 0; fi < (int)h->fields.size(); ++fi) {
+    if (fi == fl->pos_field || fi == fl->vel_field || fi == fl->acc_field) continue;
+    for (int c = 0; c < h->fields[fi].ncomp; ++c) {
+      const int pl = h->fields[fi].first_plane + c;
+      g.in[g.nother] = h->planes[src][pl];
+      g.out[g.nother] = h->planes[dst][pl];
+      g.es[g.nother] = h->plane_esize[pl];
+      ++g.nother;
+    }
+  }
+  if (int r = prepare_gather_kernels()) return r;
+  const GatherKernel kern = gather_kernel(ein.tau_src != nullptr, ein.ax != nullptr);
+  const int gsz = persistent_grid((const void*)kern, kFusedBlock, kScaledTrigBytes, grid_for(h->n, kFusedBlock));
+  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(ein, eout, g, f, make_turns_k(fl->dt), nsteps,
+                                                                  grid ? keys : nullptr, ck);
+  if (int r = check_launch(who)) return r;
+  h->current = dst;
+  return SOAX_OK;
+}
+
 }  // namespace soax
+
+extern "C" int soax_permute_step_fused(soax_t h, const uint32_t* perm, const soax_flow* fl, int32_t nsteps,
+                                       int32_t grid, uint32_t* keys, void* stream) {
+  return soax::permute_step_fused(h, perm, fl, nsteps, grid, keys, stream);
+}
 
 extern "C" int soax_step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream) {
   return soax::step_fused(h, fl, nsteps, 0, nullptr, stream, "soax_step_fused");

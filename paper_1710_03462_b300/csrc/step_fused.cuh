@@ -7,6 +7,7 @@
 
 #include "cell_key.cuh"
 #include "rk2_turns.cuh"
+#include "soax_internal.h"
 #include "step_core.cuh"
 
 namespace soax {
@@ -141,6 +142,63 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused(EnsArgs e, FlowK
   const StepC kc = make_stepc(e, f);
   const TrigScaled tg{s_tab3};
   fused_loop<PPT, TAU, ACC>(e, kc, tk, tg, nsteps, keys, ck);
+}
+
+// soax_permute_step_fused: the permute-gather of every plane fused into the step's one
+// pass.  Particle i of the output (the other buffer set) is particle perm[i] of the input
+// (the live set): its position and velocity are gathered, stepped and stored at i, its
+// other planes copied to i, so the planes are read and written once for the permute and
+// all the steps together.
+struct GatherArgs {
+  const uint32_t* perm;
+  int* status;                  // a perm entry >= n is recorded here (element 0 is used)
+  int nother;                   // planes copied unchanged (everything but pos, vel, acc)
+  const void* in[kMaxPlanes];
+  void* out[kMaxPlanes];
+  int es[kMaxPlanes];           // element size: 1, 4 or 8 bytes
+};
+
+template <int BLOCK, int MINB, bool TAU, bool ACC>
+__global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused_gather(EnsArgs ein, EnsArgs eout, GatherArgs g,
+                                                                       FlowK f, TurnsK tk, int nsteps,
+                                                                       uint32_t* __restrict__ keys, CellKeyK ck) {
+  extern __shared__ float4 s_tab3[];
+  load_scaled_trig_tables(s_tab3, ff_from2(ein.Af), ff_from2(ein.Bf), ff_from2(ein.Cf));
+  const StepC kc = make_stepc(ein, f);
+  const TrigScaled tg{s_tab3};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ein.n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t src = g.perm[i];
+    if (src >= ein.n) {
+      atomicExch(g.status, (int)SOAX_EINVAL);
+      src = 0;
+    }
+    for (int p = 0; p < g.nother; ++p) {
+      const int es = g.es[p];
+      if (es == 8)
+        static_cast<unsigned long long*>(g.out[p])[i] = static_cast<const unsigned long long*>(g.in[p])[src];
+      else if (es == 4)
+        static_cast<uint32_t*>(g.out[p])[i] = static_cast<const uint32_t*>(g.in[p])[src];
+      else
+        static_cast<uint8_t*>(g.out[p])[i] = static_cast<const uint8_t*>(g.in[p])[src];
+    }
+    uint64_t T[3] = {to_turns(ein.px[src]), to_turns(ein.py[src]), to_turns(ein.pz[src])};
+    float v[3] = {ein.vx[src], ein.vy[src], ein.vz[src]}, a[3] = {0.f, 0.f, 0.f};
+    StepC k = kc;
+    if constexpr (TAU) set_inv_tau(k, particle_inv_tau<true>(ein, src));
+    for (int s = 0; s < nsteps; ++s) {
+      if (near_shift(k, v))
+        rk2_step_turns<ACC, true>(k, tk, tg, T, v, a);
+      else
+        rk2_step_turns<ACC, false>(k, tk, tg, T, v, a);
+    }
+    const double x = turns_to_x(T[0]), y = turns_to_x(T[1]), z = turns_to_x(T[2]);
+    eout.px[i] = x;
+    eout.py[i] = y;
+    eout.pz[i] = z;
+    if (keys) keys[i] = cell_key(x, y, z, ck);
+    eout.vx[i] = v[0]; eout.vy[i] = v[1]; eout.vz[i] = v[2];
+    if constexpr (ACC) { eout.ax[i] = a[0]; eout.ay[i] = a[1]; eout.az[i] = a[2]; }
+  }
 }
 
 }  // namespace soax

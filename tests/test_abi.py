@@ -110,6 +110,14 @@ def test_empty_handle_is_a_no_op():
     assert L.soax_step_fused_keys(h, C.byref(fl), 1, 32, None, None) == 0
     assert L.soax_sort_by_keys(h, 0, None, None, 0, None) == -1
     assert L.soax_sort_by_keys(h, 32, None, None, 0, None) == 0
+    assert L.soax_sort_perm(h, 0, None, None, 0, None) == -1
+    assert L.soax_sort_perm(h, 32, None, None, 0, None) == 0
+    cur = C.c_int32()
+    assert L.soax_permute_step_fused(h, None, C.byref(fl), 1, 2000, None, None) == -1
+    assert L.soax_permute_step_fused(h, None, C.byref(fl), -1, 0, None, None) == -1
+    assert L.soax_current(h, C.byref(cur)) == 0 and cur.value == 0
+    assert L.soax_permute_step_fused(h, None, C.byref(fl), 1, 0, None, None) == 0  # n = 0: flips only
+    assert L.soax_current(h, C.byref(cur)) == 0 and cur.value == 1
     assert L.soax_step_fused(h, C.byref(fl), 3, None) == 0
     assert L.soax_soa_to_aos(h, None, None) == 0
     L.soax_destroy(h)

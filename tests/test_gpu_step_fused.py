@@ -220,3 +220,76 @@ def test_sort_by_keys_equals_sort_by_cell():
             assert x.tobytes() == y.tobytes()
     sk = ka.cpu().numpy().view(np.uint32)
     assert np.all(np.diff(sk.astype(np.int64)) >= 0)
+
+
+@pytest.mark.parametrize("schema,grid", [("basic", 32), ("wide", 64), ("basic", 0)])
+def test_permute_step_fused_equals_permute_then_step(schema, grid):
+    """soax_permute_step_fused gives the bits of soax_permute followed by the fused step
+    (and its keys), for every field of the record, and flips the live set."""
+    n = 50003
+    if schema == "basic":
+        d, sch, f = soax_inputs.basic_set(n, 31), sx.BASIC_SCHEMA, sx.Flow(tau=0.2, dt=1e-3)
+    else:
+        d, sch = soax_inputs.wide_set(n, 32), sx.WIDE_SCHEMA
+        f = sx.Flow(dt=5e-4, tau_field="mass", tau_scale=0.1, acc="acc")
+    rng = np.random.default_rng(5)
+    perm = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
+    a = sx.Particles(sch, n)
+    b = sx.Particles(sch, n)
+    a.load(d)
+    b.load(d)
+    a.permute(perm)
+    ka = a.step_fused(f, 7, grid=grid) if grid else a.step_fused(f, 7)
+    before = b.current
+    kb = b.step_fused(f, 7, grid=grid if grid else None, perm=perm)
+    assert b.current == 1 - before
+    ga, gb = a.numpy(), b.numpy()
+    for k in ga:
+        for x, y in zip(ga[k], gb[k]):
+            assert x.tobytes() == y.tobytes(), k
+    if grid:
+        assert torch.equal(ka[:n], kb[:n])
+    sx.sync()
+
+
+def test_permute_step_fused_reports_bad_index():
+    """A perm entry >= n is not read: particle 0 is gathered instead and soax_sync
+    reports SOAX_EINVAL."""
+    n = 1000
+    d = soax_inputs.basic_set(n, 33)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    p.load(d)
+    perm = torch.arange(n, dtype=torch.int32, device="cuda")
+    perm[17] = n + 5
+    p.step_fused(sx.Flow(), 2, perm=perm)
+    with pytest.raises(sx.SoaxError) as err:
+        sx.sync()
+    assert err.value.code == -1
+    assert int(p.field("id")[0][17]) == 0
+
+
+def test_deferred_permute_sequence_equals_sort_by_keys():
+    """The bench's sequence -- each fused step gathers by the permutation the previous
+    sort left, then sort_perm -- ends, after one last permute, in the state of fused steps
+    with keys each followed by sort_by_keys."""
+    n, grid = 120001, 32
+    d = soax_inputs.basic_set(n, 34)
+    f = sx.Flow(tau=0.1, dt=1e-3)
+    a = sx.Particles(sx.BASIC_SCHEMA, n)
+    b = sx.Particles(sx.BASIC_SCHEMA, n)
+    a.load(d)
+    b.load(d)
+    wa, wb = a.sort_workspace(grid), b.sort_workspace(grid)
+    ka = torch.empty(n, dtype=torch.int32, device="cuda")
+    kb = torch.empty(n, dtype=torch.int32, device="cuda")
+    perm = None
+    for _ in range(4):
+        a.step_fused(f, 10, grid=grid, keys=ka)
+        a.sort_by_keys(grid, ka, wa)
+        b.step_fused(f, 10, grid=grid, keys=kb, perm=perm)
+        _, perm = b.sort_perm(grid, kb, wb)
+    b.permute(perm)
+    ga, gb = a.numpy(), b.numpy()
+    for k in ga:
+        for x, y in zip(ga[k], gb[k]):
+            assert x.tobytes() == y.tobytes(), k
