@@ -9,6 +9,7 @@
 // the fused form (tune.fuse_steps), all steps of the call in registers with
 // soax_step_fused's per-particle function.  Every launch shape of a form gives the same
 // bits as the matching single-ensemble call.
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -19,7 +20,8 @@
 
 namespace soax {
 
-TurnsK make_turns_k(double dt);
+TurnsK make_turns_k(double dt, double umax);
+double amplitude_bound(const soax_flow* fl);
 
 constexpr int kMaxEnsembles = 4096;
 
@@ -186,6 +188,7 @@ static std::map<void*, std::vector<char>> g_plans;
 struct Prepared {
   int64_t ntiles = 0;
   FlowK f{};
+  double umax = 0.0;  // the largest amplitude bound over the ensembles
   BatchedKernel kern = nullptr;
   BatchedFusedKernel fkern = nullptr;
   int* status = nullptr;
@@ -216,6 +219,7 @@ static int prepare(const soax_t* hs, const soax_flow* fls, int nens, const soax_
     else if (fk.dt != out->f.dt)
       return fail(SOAX_EINVAL, "soax_step_batched: every ensemble must use the same dt");
     prefix[k + 1] = prefix[k] + (hs[k]->n + tile_parts - 1) / tile_parts;
+    out->umax = std::fmax(out->umax, amplitude_bound(&fls[k]));
   }
   out->ntiles = prefix[nens];
   hdr->magic = kPlanMagic;
@@ -306,7 +310,7 @@ extern "C" int soax_step_batched(const soax_t* hs, const soax_flow* fls, int32_t
   const int64_t* prefix = reinterpret_cast<const int64_t*>(static_cast<char*>(ws) + kHeaderBytes +
                                                            b256((size_t)nens * sizeof(EnsArgs)));
   if (t.fuse_steps) {
-    p.fkern<<<p.grid, p.block, p.smem, s>>>(hdr, table, prefix, nens, p.ntiles, p.f, make_turns_k(p.f.dt), nsteps,
+    p.fkern<<<p.grid, p.block, p.smem, s>>>(hdr, table, prefix, nens, p.ntiles, p.f, make_turns_k(p.f.dt, p.umax), nsteps,
                                             p.status);
     return check_launch("soax_step_batched");
   }

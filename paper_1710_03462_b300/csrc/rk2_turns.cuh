@@ -18,9 +18,11 @@
 namespace soax {
 
 // Per-launch constants of the fixed-point update: dt and dt/2 times 2^32 / 2pi as float
-// pairs, so dt vm becomes a displacement in units of 2^-32 turn with one float-pair product.
+// pairs, so dt vm becomes a displacement in units of 2^-32 turn with one float-pair
+// product; umax bounds |u_c| over the launch (|A| + |C|, |B| + |A|, |C| + |B|, largest).
 struct TurnsK {
   ff dtT, hdtT;
+  float umax;
 };
 
 // f (a displacement in units of 2^-32 turn, any magnitude) as 2^-64 turns modulo 2^64,
@@ -43,25 +45,44 @@ __device__ __forceinline__ uint64_t f_to_turns64(float f) {
   return (u >> 31) ? 0ull - r : r;
 }
 
-// T + q (mod 2^64) for a displacement q = q.h + q.l in units of 2^-32 turn.  When
-// |q.h| <= 4194000 (|dt vm| <= 6.1e-3 rad) and |q.l| < 1 the float magic-number split
-// below is exact up to the rounding of s (2^-56 turn); other displacements take
-// f_to_turns64.  The pair need not be normalised: q.l comes from sums of float-pair
-// products, and where vm = v + (dt/2) a1 cancels it can be many ulps of q.h.
+// T + q (mod 2^64) for a displacement q = q.h + q.l in units of 2^-32 turn with
+// |q.h| <= 4194000 (|dt vm| <= 6.1e-3 rad) and |q.l| < 1: the float magic-number split
+// below is exact up to the rounding of s (2^-56 turn).
+__device__ __forceinline__ uint64_t turns_add_fast(uint64_t T, ff q) {
+  // t = q.h + 1.5 2^23 lies in [2^23, 2^24), where the float spacing is 1: t - 1.5 2^23
+  // is rint(q.h), and its mantissa bits are that integer plus 2^22.
+  const float t = __fadd_rn(q.h, 0x1.8p23f);
+  const float fq = __fsub_rn(t, 0x1.8p23f);
+  const int qi = (int)(__float_as_uint(t) - 0x4B400000u);
+  // The rest, s = q.h - rint(q.h) + q.l with |s| < 1.5, as an integer number of 2^-62
+  // turns (|s 2^30| < 2^31).
+  const float s = __fadd_rn(__fsub_rn(q.h, fq), q.l);
+  const int ri = __float2int_rn(__fmul_rn(s, 0x1p30f));
+  return T + (uint64_t)(((int64_t)qi << 32) + ((int64_t)ri << 2));
+}
+
+// T + q (mod 2^64) for any displacement: turns_add_fast where its bounds hold, else the
+// exact conversion of both floats (f_to_turns64).  The pair need not be normalised: q.l
+// comes from sums of float-pair products, and where vm = v + (dt/2) a1 cancels it can be
+// many ulps of q.h.
 __device__ __forceinline__ uint64_t turns_add(uint64_t T, ff q) {
-  if (fabsf(q.h) <= 4194000.0f && fabsf(q.l) < 1.0f) {
-    // t = q.h + 1.5 2^23 lies in [2^23, 2^24), where the float spacing is 1: t - 1.5 2^23
-    // is rint(q.h), and its mantissa bits are that integer plus 2^22.
-    const float t = __fadd_rn(q.h, 0x1.8p23f);
-    const float fq = __fsub_rn(t, 0x1.8p23f);
-    const int qi = (int)(__float_as_uint(t) - 0x4B400000u);
-    // The rest, s = q.h - rint(q.h) + q.l with |s| < 1.5, as an integer number of 2^-62
-    // turns (|s 2^30| < 2^31).
-    const float s = __fadd_rn(__fsub_rn(q.h, fq), q.l);
-    const int ri = __float2int_rn(__fmul_rn(s, 0x1p30f));
-    return T + (uint64_t)(((int64_t)qi << 32) + ((int64_t)ri << 2));
-  }
+  if (fabsf(q.h) <= 4194000.0f && fabsf(q.l) < 1.0f) return turns_add_fast(T, q);
   return T + f_to_turns64(q.h) + f_to_turns64(q.l);
+}
+
+// True when every step of a particle whose speeds are within the shift series
+// (|v_c| <= vnear) has a displacement within turns_add_fast's bounds, so such steps need
+// no check.  With hs = (dt/2)/tau and |u_c| <= umax:
+//   vm = (1 - hs) v + hs u(x),  |vm| <= |1 - hs| vnear + hs umax = b;
+//   |q.h| <= dtT b (1 + 2^-23);  |q.l| <= 2^-24 dtT (3 b + 2 hs (umax + vnear))
+// (q = dtT vm as a float pair; vm.l holds the two-sum error of vm and the low part of
+// hs w0).  Both are taken with margins and compared with 4194000 and 1.
+__device__ __forceinline__ bool fast_positions(const StepC& k, const TurnsK& tk) {
+  const float hs = k.hs.h;
+  const float b = __fmaf_rn(fabsf(1.0f - hs) + 1e-3f, k.vnear, hs * tk.umax) * 1.001f;
+  const float qh = tk.dtT.h * b * 1.001f;
+  const float ql = tk.dtT.h * 0x1p-24f * (3.0f * b + 2.0f * hs * (tk.umax + k.vnear)) * 1.1f;
+  return qh <= 4194000.0f && ql < 1.0f;
 }
 
 // x = 2 pi T 2^-64 in binary64, wrapped once into [0, 2pi).  T = Th 2^32 + Tl; 2 pi 2^-32
@@ -75,9 +96,12 @@ __device__ __forceinline__ double turns_to_x(uint64_t T) {
 }
 
 // One step of the particle (T, v): the arithmetic of rk2_step_fast, with the midpoint of a
-// long shift and the new position formed in turns.  NEAR: every |v_c| <= vnear (checked by
-// the caller); otherwise each coordinate takes the series or the table at the midpoint.
-template <bool ACC, bool NEAR, class Trig>
+// long shift and the new position formed in turns.  NEAR: every |v_c| <= vnear and
+// fast_positions hold (checked by the caller); otherwise each coordinate takes the series
+// or the table at the midpoint, and each displacement is checked.
+// FAST (with NEAR): fast_positions holds, so the position update takes turns_add_fast
+// without a check (the same bits as turns_add there).
+template <bool ACC, bool NEAR, class Trig, bool FAST = NEAR>
 __device__ __forceinline__ void rk2_step_turns(const StepC& k, const TurnsK& tk, const Trig& trig, uint64_t T[3],
                                                float v[3], float a2out[3]) {
   ff P[3], Q[3], dP[3], dQ[3];
@@ -110,7 +134,10 @@ __device__ __forceinline__ void rk2_step_turns(const StepC& k, const TurnsK& tk,
       const ff a2 = ff_mul(k.s, w1);
       a2out[c] = __fadd_rn(a2.h, a2.l);
     }
-    T[c] = turns_add(T[c], ff_mul(tk.dtT, vm));
+    if constexpr (FAST)
+      T[c] = turns_add_fast(T[c], ff_mul(tk.dtT, vm));
+    else
+      T[c] = turns_add(T[c], ff_mul(tk.dtT, vm));
   }
   v[0] = vn[0];
   v[1] = vn[1];

@@ -1,4 +1,5 @@
 // soax_step_fused: nsteps midpoint-RK2 steps per particle in one pass over the planes.
+#include <cmath>
 #include <mutex>
 
 #include "soax_internal.h"
@@ -46,13 +47,21 @@ static int prepare_fused_kernels() {
   return SOAX_OK;
 }
 
-TurnsK make_turns_k(double dt) {
+// umax: a bound of |u_c| for every particle of the launch (the largest sum of two
+// amplitudes), used by fast_positions.
+TurnsK make_turns_k(double dt, double umax) {
   const double turn32 = 4294967296.0 / SOAX_TWO_PI_HOST;  // 2^32 / 2pi
   TurnsK t;
   const float2 a = split_ff(dt * turn32), b = split_ff(0.5 * dt * turn32);
   t.dtT = ff{a.x, a.y};
   t.hdtT = ff{b.x, b.y};
+  t.umax = (float)(umax * (1.0 + 1e-6));
   return t;
+}
+
+double amplitude_bound(const soax_flow* fl) {
+  const double a = std::fabs(fl->A), b = std::fabs(fl->B), c = std::fabs(fl->C);
+  return std::fmax(a + c, std::fmax(b + a, c + b));
 }
 
 static int step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t grid, uint32_t* keys, void* stream,
@@ -75,7 +84,7 @@ static int step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t gri
   const FusedKernel kern = fused_kernel(e.tau_src != nullptr, e.ax != nullptr);
   const int gsz = persistent_grid((const void*)kern, kFusedBlock, kScaledTrigBytes,
                                   grid_for((h->n + kFusedPPT - 1) / kFusedPPT, kFusedBlock));
-  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(e, f, make_turns_k(fl->dt), nsteps,
+  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(e, f, make_turns_k(fl->dt, amplitude_bound(fl)), nsteps,
                                                                    grid ? keys : nullptr, ck);
   return check_launch(who);
 }
@@ -156,7 +165,7 @@ static int permute_step_fused(soax_t h, const uint32_t* perm, const soax_flow* f
   if (int r = prepare_gather_kernels()) return r;
   const GatherKernel kern = gather_kernel(ein.tau_src != nullptr, ein.ax != nullptr);
   const int gsz = persistent_grid((const void*)kern, kFusedBlock, kScaledTrigBytes, grid_for(h->n, kFusedBlock));
-  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(ein, eout, g, f, make_turns_k(fl->dt), nsteps,
+  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(ein, eout, g, f, make_turns_k(fl->dt, amplitude_bound(fl)), nsteps,
                                                                   grid ? keys : nullptr, ck);
   if (int r = check_launch(who)) return r;
   h->current = dst;

@@ -36,7 +36,8 @@ __device__ __forceinline__ void fused_tail(const EnsArgs& e, const StepC& kc, co
 
 // The PPT particles i0..i0+PPT-1 (all < n): one vectorised load and store of each plane,
 // nsteps steps in between (nsteps >= 1).  A group whose speeds are all within the shift
-// series (near_shift) runs straight-line code for that step.
+// series (near_shift), with displacements that need no check (fast_positions), runs
+// straight-line code for that step.
 template <int PPT, bool TAU, bool ACC, class Trig>
 __device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, const TurnsK& tk, const Trig& trig,
                                             int64_t i0, int nsteps, uint32_t* keys, const CellKeyK& ck) {
@@ -60,8 +61,16 @@ __device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, c
     if constexpr (TAU) sj[j] = particle_inv_tau<true>(e, i0 + j);
   }
   StepC k = kc;
+  // Whether the displacements of steps within the shift series need no check (fixed for
+  // the call: it depends on tau, dt and the amplitudes only).
+  bool fast = true;
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    if constexpr (TAU) set_inv_tau(k, sj[j]);
+    fast = fast && fast_positions(k, tk);
+  }
   for (int s = 0; s < nsteps; ++s) {
-    bool near = true;
+    bool near = fast;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) near = near && near_shift(k, v[j]);
     if (near) {
@@ -185,8 +194,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused_gather(EnsArgs e
     float v[3] = {ein.vx[src], ein.vy[src], ein.vz[src]}, a[3] = {0.f, 0.f, 0.f};
     StepC k = kc;
     if constexpr (TAU) set_inv_tau(k, particle_inv_tau<true>(ein, src));
+    const bool fast = fast_positions(k, tk);
     for (int s = 0; s < nsteps; ++s) {
-      if (near_shift(k, v))
+      if (fast && near_shift(k, v))
         rk2_step_turns<ACC, true>(k, tk, tg, T, v, a);
       else
         rk2_step_turns<ACC, false>(k, tk, tg, T, v, a);
