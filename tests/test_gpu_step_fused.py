@@ -293,3 +293,40 @@ def test_deferred_permute_sequence_equals_sort_by_keys():
     for k in ga:
         for x, y in zip(ga[k], gb[k]):
             assert x.tobytes() == y.tobytes(), k
+
+
+def test_fused_full_size_wide_n64M_sampled():
+    """The 67,108,864-particle wide record in the fused form: one sort interval (20 steps,
+    tau from mass, acc) in one launch with the keys on the 64^3 grid, then the gather of
+    the next interval through the permutation of those keys; every 16384th particle
+    against the oracle, the keys bit-exact on the sample."""
+    w = soax_inputs.WORKLOADS["wide_n64M"]
+    n, steps, grid = w["n"], w["sort_every"], w["grid"]
+    d = soax_inputs.wide_set(n, w["seed"])
+    p = sx.Particles(sx.WIDE_SCHEMA, n)
+    p.load(d)
+    f = sx.Flow(A=w["A"], B=w["B"], C=w["C"], dt=w["dt"], tau_field="mass", tau_scale=w["tau_scale"], acc="acc")
+    keys = p.step_fused(f, steps, grid=grid)
+    idx = np.arange(3, n, 16384)
+    gpos = [t[idx].cpu().numpy() for t in p.field("pos")]
+    gvel = [t[idx].cpu().numpy() for t in p.field("vel")]
+    x0 = [np.ascontiguousarray(a[idx]) for a in d["pos"]]
+    v0 = [np.ascontiguousarray(a[idx]) for a in d["vel"]]
+    m = np.ascontiguousarray(d["mass"][0][idx])
+    opos, ovel = [a.copy() for a in x0], [a.copy() for a in v0]
+    oracle.step_soa(opos, ovel, w["A"], w["B"], w["C"], 0.0, w["dt"], steps, mass=m, tau_scale=w["tau_scale"])
+    assert_parity_fused(gpos, gvel, opos, ovel, x0, v0, w["tau_scale"] * m.astype(np.float64), w["A"], w["B"],
+                        w["C"], w["dt"], steps)
+    assert np.array_equal(keys[idx].cpu().numpy().view(np.uint32), oracle.cell_keys(*gpos, grid))
+    del d
+    ws = p.sort_workspace(grid)
+    _, perm = p.sort_perm(grid, keys, ws)
+    ids_before = p.field("id")[0].clone()
+    p.step_fused(f, 1, grid=grid, keys=keys, perm=perm)
+    sx.sync()
+    ids = p.field("id")[0]
+    assert torch.equal(ids, ids_before[perm.long()])
+    sk = keys.cpu().numpy().view(np.uint32)
+    assert sk.min() >= 0 and sk.max() < grid ** 3
+    del p, ws, keys, perm, ids_before, ids
+    torch.cuda.empty_cache()
