@@ -258,8 +258,8 @@ int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_
 int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes, void* stream);
 
 /* soax_sort_by_keys without the permute-gather: the stable permutation that sorts keys
- * (and the sorted keys) are left in ws (soax_sort_results gives their addresses); no
- * particle moves.  Pair it with soax_permute_step_fused, or soax_permute. */
+ * is left in ws (soax_sort_results gives its address; the sorted keys are not written);
+ * no particle moves.  Pair it with soax_permute_step_fused, or soax_permute. */
 int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes, void* stream);
 
 /* soax_sort_by_cell without a caller workspace.  The paper has no counterpart: this is

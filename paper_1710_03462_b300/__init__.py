@@ -261,11 +261,11 @@ class Particles:
 
     def sort_perm(self, grid, keys, ws=None, stream=None):
         """The stable permutation sorting keys, left in ws (no particle moves); returns
-        (sorted keys, perm) as int32 views into ws."""
+        (None, perm) with perm an int32 view into ws (the sorted keys are not written)."""
         ws = self.sort_workspace(grid) if ws is None else ws
         _check(lib().soax_sort_perm(self.h, int(grid), _ptr(keys), _ptr(ws), ws.numel(), _stream(stream)),
                "soax_sort_perm")
-        return self.sort_results(grid, ws)
+        return None, self.sort_results(grid, ws)[1]
 
     def sort_results(self, grid, ws):
         k, p = C.c_void_p(), C.c_void_p()

@@ -501,9 +501,8 @@ extern "C" int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void
   if (!ws || ws_bytes < w.total) return fail(SOAX_ENOMEM, "soax_sort_perm: workspace too small");
   if (!aligned16(ws)) return fail(SOAX_EALIGN, "soax_sort_perm: workspace not 16-byte aligned");
   char* base = static_cast<char*>(ws);
-  return soax_radix_sort_pairs(keys, nullptr, reinterpret_cast<uint32_t*>(base + w.off_skeys),
-                               reinterpret_cast<uint32_t*>(base + w.off_perm), h->n, key_bits_for_grid(grid),
-                               base + w.off_radix, w.rp.total, stream);
+  return soax_radix_sort_pairs(keys, nullptr, nullptr, reinterpret_cast<uint32_t*>(base + w.off_perm), h->n,
+                               key_bits_for_grid(grid), base + w.off_radix, w.rp.total, stream);
 }
 
 extern "C" int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes,

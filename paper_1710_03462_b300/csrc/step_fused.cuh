@@ -175,11 +175,27 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused_gather(EnsArgs e
   load_scaled_trig_tables(s_tab3, ff_from2(ein.Af), ff_from2(ein.Bf), ff_from2(ein.Cf));
   const StepC kc = make_stepc(ein, f);
   const TrigScaled tg{s_tab3};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ein.n; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t src = g.perm[i];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t src_next = i < ein.n ? g.perm[i] : 0u;
+  for (; i < ein.n; i += stride) {
+    int64_t src = src_next;
     if (src >= ein.n) {
       atomicExch(g.status, (int)SOAX_EINVAL);
       src = 0;
+    }
+    // The next particle's source: read its perm entry now and start moving its position
+    // and velocity into L2, so that its gather does not wait on HBM after this particle's
+    // steps.  An entry >= n is prefetched as 0 (and reported when it is used).
+    if (i + stride < ein.n) {
+      src_next = g.perm[i + stride];
+      const int64_t pf = src_next < ein.n ? (int64_t)src_next : 0;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ein.px + pf));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ein.py + pf));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ein.pz + pf));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ein.vx + pf));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ein.vy + pf));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ein.vz + pf));
     }
     for (int p = 0; p < g.nother; ++p) {
       const int es = g.es[p];
