@@ -208,14 +208,20 @@ struct TrigUnscaled {
 
 // a sin and a cos of theta_k + r from the entry (S, C) = (a sin theta_k, a cos theta_k)
 // of a table scaled by the amplitude a (a = 1: the plain table), |r| <= pi/2048.
+// m = -r^2/2 as a float pair, and from it cos r - 1 = m + m^2/6 and sin r = r + m r/3
+// (r^6/720 < 2e-20 and r^5/120 < 8e-17 dropped; m^2/6 < 3e-13 and m r/3 < 6e-10 are
+// exact enough in float: errors < 4e-17).  -r.h/2 is exact, so two_prod(r.h, -r.h/2)
+// is r.h^2 (-1/2) exactly, and -r.h r.l adds the cross term.
+__device__ __forceinline__ void series_terms(ff r, ff& cm, ff& sr) {
+  ff m = two_prod(r.h, __fmul_rn(-0.5f, r.h));
+  m.l = __fmaf_rn(-r.h, r.l, m.l);
+  cm = ff{m.h, __fmaf_rn(__fmul_rn(m.h, 1.0f / 6.0f), m.h, m.l)};
+  sr = ff{r.h, __fmaf_rn(__fmul_rn(m.h, r.h), 1.0f / 3.0f, r.l)};
+}
+
 __device__ __forceinline__ void sincos_tab(const float4 t, ff r, ff& s, ff& c) {
-  ff p = two_prod(r.h, r.h);  // r^2
-  p.l = __fmaf_rn(__fmul_rn(2.0f, r.h), r.l, p.l);
-  // cos r - 1 = -r^2/2 + r^4/24 (r^6/720 < 2e-20 dropped; r^4/24 < 3e-13 in float)
-  const ff cm = {__fmul_rn(-0.5f, p.h), __fmaf_rn(__fmul_rn(p.h, p.h), 1.0f / 24.0f, __fmul_rn(-0.5f, p.l))};
-  // sin r = r - r^3/6 (r^3/6 < 6e-10 is exact enough in float: error < 4e-17;
-  // r^5/120 < 8e-17 dropped)
-  const ff sr = {r.h, __fsub_rn(r.l, __fmul_rn(__fmul_rn(p.h, r.h), 1.0f / 6.0f))};
+  ff cm, sr;  // cos r - 1, sin r
+  series_terms(r, cm, sr);
   // Every entry of the plain table is 0 or at least sin(2pi/2048) = 3.07e-3 in magnitude
   // while |r| <= pi/2048 = 1.54e-3, so in each sum below the first term is zero or the
   // larger one: |S|, |C| > |C sr|, |S sr| >= 3.07e-3 |r| > r^2/2 >= |S cm|, |C cm|.  A
@@ -230,22 +236,18 @@ __device__ __forceinline__ void sincos_tab(const float4 t, ff r, ff& s, ff& c) {
 //   sin(a + d) - sin a = cos a sin d + sin a (cos d - 1)  -> qs
 //   cos(a + d) - cos a = cos a (cos d - 1) - sin a sin d  -> qc
 __device__ __forceinline__ void sincos_delta(ff sa, ff ca, ff d, ff& qs, ff& qc) {
-  ff d2 = two_prod(d.h, d.h);
-  d2.l = __fmaf_rn(__fmul_rn(2.0f, d.h), d.l, d2.l);
-  // cos d - 1 = -d^2/2 + d^4/24;  sin d = d - d^3/6 (d^5/120 < 2e-16 relative, dropped)
-  const ff cmd = {__fmul_rn(-0.5f, d2.h), __fmaf_rn(__fmul_rn(d2.h, d2.h), 1.0f / 24.0f, __fmul_rn(-0.5f, d2.l))};
-  const ff sd = {d.h, __fsub_rn(d.l, __fmul_rn(__fmul_rn(d2.h, d.h), 1.0f / 6.0f))};
+  // cos d - 1 and sin d by the series of series_terms (d^5/120 < 2e-16 relative, dropped)
+  ff cmd, sd;
+  series_terms(d, cmd, sd);
   qs = ff_add(ff_mul(ca, sd), ff_mul(sa, cmd));
   qc = ff_sub(ff_mul(ca, cmd), ff_mul(sa, sd));
 }
 
 // sin and cos of a + d from those of a, |d| <= ~2e-3.
 __device__ __forceinline__ void sincos_shift(ff sa, ff ca, ff d, ff& s, ff& c) {
-  ff d2 = two_prod(d.h, d.h);
-  d2.l = __fmaf_rn(__fmul_rn(2.0f, d.h), d.l, d2.l);
-  // cos d - 1 = -d^2/2 + d^4/24;  sin d = d - d^3/6 (d^5/120 < 2e-16 relative, dropped)
-  const ff cmd = {__fmul_rn(-0.5f, d2.h), __fmaf_rn(__fmul_rn(d2.h, d2.h), 1.0f / 24.0f, __fmul_rn(-0.5f, d2.l))};
-  const ff sd = {d.h, __fsub_rn(d.l, __fmul_rn(__fmul_rn(d2.h, d.h), 1.0f / 6.0f))};
+  // cos d - 1 and sin d by the series of series_terms (d^5/120 < 2e-16 relative, dropped)
+  ff cmd, sd;
+  series_terms(d, cmd, sd);
   s = ff_add(sa, ff_add(ff_mul(ca, sd), ff_mul(sa, cmd)));
   c = ff_add(ca, ff_sub(ff_mul(ca, cmd), ff_mul(sa, sd)));
 }
