@@ -304,21 +304,34 @@ def run_soax(args):
     tot_units, max_el = aggregate(units, elapsed, dev)
 
     # e2e through the public API with host buffers: the state goes up and comes back
-    # every bench step (pinned memory, one async copy per plane).
+    # every bench step (pinned memory, one async copy per plane).  Uploads run on one copy
+    # stream, downloads on another, so the link's two directions work at once: plane q's
+    # upload for step k + 1 waits only for plane q's download of step k (the same host
+    # buffer and device plane), and the step waits for all of its uploads.
     host = {k: [torch.from_numpy(a).pin_memory() for a in v] for k, v in d.items()}
     e2e_steps = max(1, min(args.steps, 5))
     h2d = sum(t.numel() * t.element_size() for v in host.values() for t in v)
+    planes = [(k, c) for k, v in host.items() for c in range(len(v))]
+    s_up, s_dn = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    down = {}
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for k, v in host.items():
-            for c, t in enumerate(v):
-                p.field(k)[c].copy_(t, non_blocking=True)
+        with torch.cuda.stream(s_up):
+            for k, c in planes:
+                if (k, c) in down:
+                    s_up.wait_event(down[(k, c)])
+                p.field(k)[c].copy_(host[k][c], non_blocking=True)
+        stream.wait_stream(s_up)
         bench_step()
-        for k, v in host.items():
-            for c, t in enumerate(v):
-                t.copy_(p.field(k)[c], non_blocking=True)
-        torch.cuda.synchronize(dev)
+        s_dn.wait_stream(stream)
+        with torch.cuda.stream(s_dn):
+            for k, c in planes:
+                host[k][c].copy_(p.field(k)[c], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s_dn)
+                down[(k, c)] = ev
+    torch.cuda.synchronize(dev)
     e2e_el = time.perf_counter() - t0
     e2e_units, e2e_max = aggregate(n * RK2_PER_STEP * e2e_steps, e2e_el, dev)
 
@@ -352,7 +365,9 @@ def run_soax(args):
                      "launch_ms": statistics.mean(fused_ms)},
         "sort_ms": statistics.mean(sort_ms),
         "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": h2d, "steps": e2e_steps},
+                "d2h_bytes_per_step": h2d, "steps": e2e_steps,
+                "copies": "per plane, uploads and downloads on two streams (step k's download of a plane "
+                          "overlaps step k+1's uploads of the others)"},
         "gpu_launches": args.steps * (1 + sort_launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu_baseline(n) if world == 1 or rank == 0 else None,
