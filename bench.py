@@ -457,14 +457,17 @@ def secondary_rows(sx, torch, p, d, dev):
     reset()
     t_plain = _time(torch, lambda: pa.step(fa, K))
     reset()
+    t_plain_fused = _time(torch, lambda: pa.step_fused(fa, K))
+    reset()
 
     def fwd_adj():
         pa.step_checkpointed(fa, K, C, wsa)
         _, xb = pa.minimage_loss(xt, wsa)
         pa.step_adjoint(fa, K, C, wsa, xb)
     t_fa = _time(torch, fwd_adj)
-    rows["fwd_adjoint"] = {"n": wa["n"], "K": K, "ckpt_every": C, "plain_ms": t_plain * 1e3, "fwd_adj_ms": t_fa * 1e3,
-                           "ratio_vs_plain": t_fa / t_plain}
+    rows["fwd_adjoint"] = {"n": wa["n"], "K": K, "ckpt_every": C, "plain_ms": t_plain * 1e3,
+                           "plain_fused_ms": t_plain_fused * 1e3, "fwd_adj_ms": t_fa * 1e3,
+                           "ratio_vs_plain": t_fa / t_plain, "ratio_vs_plain_fused": t_fa / t_plain_fused}
     del pa, wsa, xt
     torch.cuda.empty_cache()
     # Batched: 512 uneven ensembles, a few steps, vs 512 plain launches per step.

@@ -315,8 +315,9 @@ int soax_euler_aos(void* rec, int64_t n, int64_t record_bytes, int64_t x_off, in
 /* Workspace bytes for K steps with a checkpoint every ckpt_every steps. */
 int soax_adjoint_workspace_bytes(soax_t h, int32_t K, int32_t ckpt_every, size_t* bytes);
 
-/* Forward: K steps in place (bit-identical to soax_step), saving the state at steps
- * 0, ckpt_every, 2*ckpt_every, ... into ws.  tau_field must be -1. */
+/* Forward: K steps in place with soax_step_fused's arithmetic (bit-identical to
+ * soax_step_fused(h, fl, K)), saving the state (position as fixed-point turns, velocity)
+ * at steps 0, ckpt_every, 2*ckpt_every, ... into ws.  tau_field must be -1. */
 int soax_step_checkpointed(soax_t h, const soax_flow* fl, int32_t K, int32_t ckpt_every, void* ws,
                            size_t ws_bytes, void* stream);
 

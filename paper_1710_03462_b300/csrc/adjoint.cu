@@ -2,20 +2,29 @@
 // minimum-image loss that seeds it.
 //
 // Every particle is independent, so one thread owns one particle for the whole
-// computation.  The forward keeps the particle in registers for all K steps and writes
-// its state every C steps (checkpoint j = state before step j*C).  The reverse walks the
-// segments backwards: it recomputes a segment from its checkpoint, pushing the C
-// states on a per-particle stack in the workspace (coalesced [step][plane][particle]
-// layout), then applies the reverse step C times.  Parameter gradients are reduced in a
-// fixed order (per-block tree, then one block over the block partials), so the result
-// is bit-reproducible.
+// computation.  The forward keeps the particle in registers for all K steps, with the
+// arithmetic of soax_step_fused (position as fixed-point turns T between steps), and
+// writes its state (T, v) every C steps (checkpoint j = state before step j*C).  The
+// reverse walks the segments backwards: it recomputes a segment from its checkpoint with
+// the same per-step function (so the states are bit-identical), pushing the C states on
+// a per-particle stack in the workspace (coalesced [step][plane][particle] layout), then
+// applies the reverse step C times.  Parameter gradients are reduced in a fixed order
+// (per-block tree, then one block over the block partials), so the result is
+// bit-reproducible.
+#include <cmath>
+#include <mutex>
+
 #include "soax_internal.h"
-#include "step_core.cuh"
+#include "step_fused.cuh"
 
 namespace soax {
 
-constexpr int kAdjBlock = 128;
+constexpr int kAdjBlock = 128;      // the reverse
+constexpr int kAdjFwdBlock = 512;   // the forward (2 blocks per SM with the scaled tables)
 constexpr int kLossBlock = 256;
+
+TurnsK make_turns_k(double dt, double umax);
+double amplitude_bound(const soax_flow* fl);
 
 __host__ __device__ static inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -37,45 +46,64 @@ static AdjWs adj_plan(int64_t n, int K, int C) {
   return w;
 }
 
+// A stored state: the position as fixed-point turns (3 u64 planes) and the velocity.
 struct StateRef {
-  double* x[3];
+  uint64_t* T[3];
   float* v[3];
 };
 
 __device__ __forceinline__ StateRef state_at(char* base, size_t sb, int64_t n, int j) {
   char* p = base + (size_t)j * sb;
   StateRef r;
-  double* xs = reinterpret_cast<double*>(p);
+  uint64_t* ts = reinterpret_cast<uint64_t*>(p);
   float* vs = reinterpret_cast<float*>(p + a256((size_t)n * 24));
   for (int c = 0; c < 3; ++c) {
-    r.x[c] = xs + (size_t)c * n;
+    r.T[c] = ts + (size_t)c * n;
     r.v[c] = vs + (size_t)c * n;
   }
   return r;
 }
 
-__global__ void __launch_bounds__(kAdjBlock) k_adj_forward(EnsArgs e, FlowK f, int K, int C, char* ckpt, size_t sb) {
-  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
-  load_trig_table(s_tab);
+// One step of the forward and of the recompute alike (soax_step_fused's choice of path,
+// so the same bits).
+template <bool ACC, class Trig>
+__device__ __forceinline__ void adj_step(const StepC& k, const TurnsK& tk, const Trig& tg, bool fast, uint64_t T[3],
+                                         float v[3], float a[3]) {
+  if (fast && near_shift(k, v))
+    rk2_step_turns<ACC, true>(k, tk, tg, T, v, a);
+  else
+    rk2_step_turns<ACC, false>(k, tk, tg, T, v, a);
+}
+
+template <bool ACC>
+__global__ void __launch_bounds__(kAdjFwdBlock, 2) k_adj_forward(EnsArgs e, FlowK f, TurnsK tk, int K, int C,
+                                                                  char* ckpt, size_t sb) {
+  extern __shared__ float4 s_tab3[];
+  load_scaled_trig_tables(s_tab3, ff_from2(e.Af), ff_from2(e.Bf), ff_from2(e.Cf));
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= e.n) return;
-  const StepC k = make_stepc(e, f, i);
-  const TrigUnscaled tg = trig_unscaled(s_tab, e);
-  double x[3] = {e.px[i], e.py[i], e.pz[i]};
+  const StepC k = make_stepc(e, f);
+  const TrigScaled tg{s_tab3};
+  const bool fast = fast_positions(k, tk);
+  uint64_t T[3] = {to_turns(e.px[i]), to_turns(e.py[i]), to_turns(e.pz[i])};
   float v[3] = {e.vx[i], e.vy[i], e.vz[i]}, a[3] = {0.f, 0.f, 0.f};
   for (int s = 0; s < K; ++s) {
     if (s % C == 0) {
       StateRef r = state_at(ckpt, sb, e.n, s / C);
       for (int c = 0; c < 3; ++c) {
-        r.x[c][i] = x[c];
+        r.T[c][i] = T[c];
         r.v[c][i] = v[c];
       }
     }
-    rk2_step<true>(k, tg, x, v, a);
+    adj_step<ACC>(k, tk, tg, fast, T, v, a);
   }
-  e.px[i] = x[0]; e.py[i] = x[1]; e.pz[i] = x[2];
+  e.px[i] = turns_to_x(T[0]);
+  e.py[i] = turns_to_x(T[1]);
+  e.pz[i] = turns_to_x(T[2]);
   e.vx[i] = v[0]; e.vy[i] = v[1]; e.vz[i] = v[2];
-  if (e.ax && K > 0) { e.ax[i] = a[0]; e.ay[i] = a[1]; e.az[i] = a[2]; }
+  if constexpr (ACC) {
+    if (K > 0) { e.ax[i] = a[0]; e.ay[i] = a[1]; e.az[i] = a[2]; }
+  }
 }
 
 // binary64 <-> float pair (once per particle, outside the step loop).
@@ -107,15 +135,18 @@ __device__ __forceinline__ void block_reduce_fixed(double (&v)[NV], double* out)
     for (int k = 0; k < NV; ++k) out[k] = red[k][0];
 }
 
-__global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, int K, int C, int nck, char* ckpt,
-                                                          char* stack, size_t sb, AdjIO io, double* partials) {
+__global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, TurnsK tk, int K, int C, int nck,
+                                                          char* ckpt, char* stack, size_t sb, AdjIO io,
+                                                          double* partials) {
   __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
   load_trig_table(s_tab);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double th[4] = {0.0, 0.0, 0.0, 0.0};
   if (i < e.n) {
     const StepC k = make_stepc(e, f, i);
+    // The plain table scaled per lookup gives the bits of the forward's scaled tables.
     const TrigUnscaled tg = trig_unscaled(s_tab, e);
+    const bool fast = fast_positions(k, tk);
     ff xb[3], vb[3], tf[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int c = 0; c < 3; ++c) {
       xb[c] = d2ff(io.xbK[c][i]);
@@ -125,27 +156,27 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, i
     for (int seg = nck - 1; seg >= 0; --seg) {
       const int s0 = seg * C, len = (K - s0 < C) ? K - s0 : C;
       StateRef ck = state_at(ckpt, sb, e.n, seg);
-      double x[3];
+      uint64_t T[3];
       float v[3];
       for (int c = 0; c < 3; ++c) {
-        x[c] = ck.x[c][i];
+        T[c] = ck.T[c][i];
         v[c] = ck.v[c][i];
       }
       for (int j = 0; j < len; ++j) {
         StateRef st = state_at(stack, sb, e.n, j);
         for (int c = 0; c < 3; ++c) {
-          st.x[c][i] = x[c];
+          st.T[c][i] = T[c];
           st.v[c][i] = v[c];
         }
-        rk2_step<false>(k, tg, x, v, a);
+        adj_step<false>(k, tk, tg, fast, T, v, a);
       }
       for (int j = len - 1; j >= 0; --j) {
         StateRef st = state_at(stack, sb, e.n, j);
         for (int c = 0; c < 3; ++c) {
-          x[c] = st.x[c][i];
+          T[c] = st.T[c][i];
           v[c] = st.v[c][i];
         }
-        rk2_reverse_fast(k, s_tab, x, v, xb, vb, tf);
+        rk2_reverse_turns(k, tk, s_tab, T, v, xb, vb, tf);
       }
     }
     for (int c = 0; c < 3; ++c) {
@@ -200,6 +231,26 @@ __global__ void __launch_bounds__(kLossBlock) k_minimage_loss(LossIO io, int64_t
   block_reduce_fixed<1, kLossBlock>(l, partials + blockIdx.x);
 }
 
+// Dynamic shared memory above 48 KB and the largest carveout for the forward, once per
+// device.
+static int prepare_adj_forward() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return cuda_fail(cudaGetLastError(), "soax_step_checkpointed: device");
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return SOAX_OK;
+  for (const void* fn : {(const void*)k_adj_forward<true>, (const void*)k_adj_forward<false>}) {
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kScaledTrigBytes);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (err != cudaSuccess) return cuda_fail(err, "soax_step_checkpointed: kernel attributes");
+  }
+  done[dev] = true;
+  return SOAX_OK;
+}
+
 static int check_ptrs3(const void* const* p, bool allow_null, const char* what) {
   if (!p) return allow_null ? SOAX_OK : fail(SOAX_EINVAL, std::string(what) + " is NULL");
   for (int c = 0; c < 3; ++c) {
@@ -239,8 +290,11 @@ extern "C" int soax_step_checkpointed(soax_t h, const soax_flow* fl, int32_t K, 
   AdjWs w;
   if (int r = adj_common(h, fl, K, ckpt_every, ws, ws_bytes, &e, &f, &w, "soax_step_checkpointed")) return r;
   if (h->n == 0 || K == 0) return SOAX_OK;
-  k_adj_forward<<<grid_for(h->n, kAdjBlock), kAdjBlock, 0, as_stream(stream)>>>(
-      e, f, K, ckpt_every, static_cast<char*>(ws) + w.off_ckpt, w.state_bytes);
+  if (int r = prepare_adj_forward()) return r;
+  const auto kern = e.ax ? k_adj_forward<true> : k_adj_forward<false>;
+  kern<<<grid_for(h->n, kAdjFwdBlock), kAdjFwdBlock, kScaledTrigBytes, as_stream(stream)>>>(
+      e, f, make_turns_k(fl->dt, amplitude_bound(fl)), K, ckpt_every, static_cast<char*>(ws) + w.off_ckpt,
+      w.state_bytes);
   return check_launch("soax_step_checkpointed");
 }
 
@@ -271,8 +325,8 @@ extern "C" int soax_step_adjoint(soax_t h, const soax_flow* fl, int32_t K, int32
   char* base = static_cast<char*>(ws);
   double* partials = reinterpret_cast<double*>(base + w.off_partials);
   const int nb = grid_for(h->n, kAdjBlock);
-  k_adj_reverse<<<nb, kAdjBlock, 0, s>>>(e, f, K, ckpt_every, w.nck, base + w.off_ckpt, base + w.off_stack,
-                                        w.state_bytes, io, partials);
+  k_adj_reverse<<<nb, kAdjBlock, 0, s>>>(e, f, make_turns_k(fl->dt, amplitude_bound(fl)), K, ckpt_every, w.nck,
+                                        base + w.off_ckpt, base + w.off_stack, w.state_bytes, io, partials);
   if (int r = check_launch("soax_step_adjoint")) return r;
   k_reduce_partials<<<1, 256, 0, s>>>(partials, nb, 4, 1.0, grad);
   return check_launch("soax_step_adjoint: reduce");

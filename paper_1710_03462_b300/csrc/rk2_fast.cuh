@@ -274,24 +274,6 @@ __device__ __forceinline__ double far_midpoint(double dt, double x, float v) {
   return xm < 0.0 ? xm + SOAX_TWO_PI : xm;
 }
 
-// sin and cos of the three coordinates of x (s0, c0) and of xm = x + (dt/2) v (s1, c1).
-__device__ __forceinline__ void step_trig(const StepC& k, const float4* __restrict__ tab, const double x[3],
-                                          const float v[3], ff s0[3], ff c0[3], ff s1[3], ff c1[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    int idx;
-    ff r;
-    reduce_angle(x[c], idx, r);
-    sincos_tab(tab[idx], r, s0[c], c0[c]);
-    if (fabsf(v[c]) <= k.vnear) {
-      sincos_shift(s0[c], c0[c], ff_mul_f(k.hdt, v[c]), s1[c], c1[c]);
-    } else {
-      reduce_angle(far_midpoint(k.dt_d, x[c], v[c]), idx, r);
-      sincos_tab(tab[idx], r, s1[c], c1[c]);
-    }
-  }
-}
-
 // u = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x) from the sines and cosines.
 __device__ __forceinline__ void abc_u(const StepC& k, const ff s[3], const ff c[3], ff u[3]) {
   u[0] = ff_add(ff_mul(k.A, s[2]), ff_mul(k.C, c[1]));
@@ -397,7 +379,8 @@ __device__ __forceinline__ void abc_vjp(const StepC& k, const ff s[3], const ff 
 
 // Reverse of one step: given the adjoints (xb, vb) of (x', v'), overwrite them with the
 // adjoints of (x, v) and accumulate d/d(A, B, C, tau) into th.  (x, v) is the state
-// before the step.  The f32 rounding of v' and the periodic wrap are differentiated as
+// before the step, given by v and the sines and cosines of x (s0, c0) and of
+// xm = x + (dt/2) v (s1, c1), unscaled.  The f32 rounding of v' and the periodic wrap are differentiated as
 // the identity.  Reverse-mode differentiation of rk2_step_fast's statements, last first:
 //   x' = x + dt vm:       xb += xb',  vmb = dt xb'
 //   v' = v + dt a2:       vb += vb',  a2b = dt vb'
@@ -408,10 +391,9 @@ __device__ __forceinline__ void abc_vjp(const StepC& k, const ff s[3], const ff 
 //   a1 = (u(x) - v) s:    u0b = s a1b,  vb -= s a1b,  sb += a1b . (u0 - v)
 //   u0 = u(x):            xb += J(x)^T u0b,  thb += (du/dtheta)(x)^T u0b
 //   s = 1/tau:            taub = -s^2 sb
-__device__ __forceinline__ void rk2_reverse_fast(const StepC& k, const float4* __restrict__ tab, const double x[3],
-                                                 const float v[3], ff xb[3], ff vb[3], ff th[4]) {
-  ff s0[3], c0[3], s1[3], c1[3], u0[3], u1[3];
-  step_trig(k, tab, x, v, s0, c0, s1, c1);
+__device__ __forceinline__ void rk2_reverse_core(const StepC& k, const ff s0[3], const ff c0[3], const ff s1[3],
+                                                 const ff c1[3], const float v[3], ff xb[3], ff vb[3], ff th[4]) {
+  ff u0[3], u1[3];
   abc_u(k, s0, c0, u0);
   abc_u(k, s1, c1, u1);
   ff d0[3], d1[3], u1b[3], vmb[3], xmb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};

@@ -7,7 +7,7 @@ import torch
 import oracle
 import paper_1710_03462_b300 as sx
 import soax_inputs
-from parity import audit_particle
+from parity import audit_particle_fused
 
 pytestmark = pytest.mark.gpu
 
@@ -38,9 +38,10 @@ def _gpu_adjoint(d, xt, K, C, th, dt=1e-3):
 def _diverged(p, d, th, K, dt=1e-3, max_frac=1e-3):
     """Particles whose forward state after K steps differs from the oracle's by more than
     f64 rounding: their f32 velocity took the other side of a rounding midpoint at some
-    step.  Each is replayed step by step (parity.audit_particle) and must be a legitimate
-    midpoint flip; their gradients then follow a slightly different trajectory and are
-    left out of the element-wise comparison."""
+    step.  The forward is soax_step_fused's arithmetic, so each is replayed on its own
+    trajectory (parity.audit_particle_fused) and must be a legitimate midpoint flip; their
+    gradients then follow a slightly different trajectory and are left out of the
+    element-wise comparison."""
     opos = [a.copy() for a in d["pos"]]
     ovel = [a.copy() for a in d["vel"]]
     oracle.step_soa(opos, ovel, *th, dt, K)
@@ -53,7 +54,8 @@ def _diverged(p, d, th, K, dt=1e-3, max_frac=1e-3):
     idx = np.flatnonzero(bad)
     assert idx.size <= max(2, max_frac * bad.size), f"{idx.size} diverged particles"
     for i in idx:
-        audit_particle([d["pos"][c][i] for c in range(3)], [d["vel"][c][i] for c in range(3)], *th[:3], th[3], dt, K)
+        audit_particle_fused([d["pos"][c][i] for c in range(3)], [d["vel"][c][i] for c in range(3)], *th[:3], th[3],
+                             dt, K)
     return bad
 
 
@@ -74,7 +76,9 @@ def test_adjoint_vs_oracle(n, K, C):
         assert np.max(np.abs(vb[c] - ovb[c])[ok]) <= 1e-9 * scale
 
 
-def test_checkpointed_forward_equals_plain_step():
+def test_checkpointed_forward_equals_fused_step():
+    """The checkpointed forward is soax_step_fused's arithmetic: the same bits as one fused
+    launch of K steps."""
     n, K = 20000, 77
     d = soax_inputs.basic_set(n, 3)
     a = sx.Particles(SCHEMA, n, shadow=False)
@@ -82,7 +86,7 @@ def test_checkpointed_forward_equals_plain_step():
     b = sx.Particles(SCHEMA, n, shadow=False)
     b.load({"pos": d["pos"], "vel": d["vel"]})
     f = sx.Flow()
-    a.step(f, K)
+    a.step_fused(f, K)
     ws = b.adjoint_workspace(K, 32)
     b.step_checkpointed(f, K, 32, ws)
     x, y = a.numpy(), b.numpy()
@@ -97,7 +101,7 @@ def test_zero_gradient_at_target():
     d = soax_inputs.basic_set(n, 4)
     t = sx.Particles(SCHEMA, n, shadow=False)
     t.load({"pos": d["pos"], "vel": d["vel"]})
-    t.step(sx.Flow(A=1.1), K)
+    t.step_fused(sx.Flow(A=1.1), K)
     xt = t.numpy()["pos"]
     ot = [a.copy() for a in d["pos"]]
     oracle.step_soa(ot, [a.copy() for a in d["vel"]], 1.1, 1.0, 1.0, 0.1, 1e-3, K)
@@ -144,7 +148,7 @@ def test_autograd_function():
     ol, oxb, ovb, og = oracle.adjoint(d["pos"], d["vel"], xt, 1.0, 0.9, 1.1, 0.1, 1e-3, K, f32v=True)
     p = sx.Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], n, shadow=False)
     p.load({"pos": d["pos"], "vel": d["vel"]})
-    p.step(sx.Flow(A=1.0, B=0.9, C=1.1, tau=0.1), K)
+    p.step_fused(sx.Flow(A=1.0, B=0.9, C=1.1, tau=0.1), K)
     ok = ~_diverged(p, d, [1.0, 0.9, 1.1, 0.1], K)
     assert np.allclose(theta.grad.cpu().numpy(), og, rtol=1e-8)
     assert np.allclose(v0.grad.cpu().numpy()[:, ok], np.stack(ovb)[:, ok], rtol=1e-8, atol=1e-14)
@@ -169,7 +173,7 @@ def test_full_size_adjoint_n1M_sampled():
     # The forward of the sampled particles, on their own, must match the full-size run.
     q = sx.Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], idx.size, shadow=False)
     q.load(sub)
-    q.step(sx.Flow(A=th[0], B=th[1], C=th[2], tau=th[3], dt=w["dt"]), K)
+    q.step_fused(sx.Flow(A=th[0], B=th[1], C=th[2], tau=th[3], dt=w["dt"]), K)
     gq, gp = q.numpy(), p.numpy()
     for c in range(3):
         assert np.array_equal(gq["pos"][c], gp["pos"][c][idx])
