@@ -89,12 +89,25 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
 }
 
 // ------------------------------------------------------------------ cell keys
+// Four particles per thread: 16-byte loads of the positions (planes and keys are 16-byte
+// aligned, so a full group of four is), one 16-byte store of the keys; the ragged end one
+// by one.
+constexpr int kKeyPPT = 4;
+
 __global__ void __launch_bounds__(256) k_cell_keys(const double* __restrict__ px, const double* __restrict__ py,
                                                    const double* __restrict__ pz, int64_t n, CellKeyK ck,
                                                    uint32_t* __restrict__ keys) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  keys[i] = cell_key(px[i], py[i], pz[i], ck);
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kKeyPPT;
+  if (i0 + kKeyPPT <= n) {
+    const double2 x0 = *reinterpret_cast<const double2*>(px + i0), x1 = *reinterpret_cast<const double2*>(px + i0 + 2);
+    const double2 y0 = *reinterpret_cast<const double2*>(py + i0), y1 = *reinterpret_cast<const double2*>(py + i0 + 2);
+    const double2 z0 = *reinterpret_cast<const double2*>(pz + i0), z1 = *reinterpret_cast<const double2*>(pz + i0 + 2);
+    *reinterpret_cast<uint4*>(keys + i0) =
+        make_uint4(cell_key(x0.x, y0.x, z0.x, ck), cell_key(x0.y, y0.y, z0.y, ck), cell_key(x1.x, y1.x, z1.x, ck),
+                   cell_key(x1.y, y1.y, z1.y, ck));
+  } else {
+    for (int64_t i = i0; i < n; ++i) keys[i] = cell_key(px[i], py[i], pz[i], ck);
+  }
 }
 
 CellKeyK make_cell_key_k(int grid) {
@@ -363,7 +376,8 @@ extern "C" int soax_cell_keys(soax_t h, int32_t pos_field, int32_t grid, uint32_
   const double* py = (const double*)h->planes[h->current][fp + 1];
   const double* pz = (const double*)h->planes[h->current][fp + 2];
   if (!px || !py || !pz) return fail(SOAX_EUNBOUND, "soax_cell_keys: position planes not bound");
-  k_cell_keys<<<grid_for(h->n, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n, make_cell_key_k(grid), keys);
+  k_cell_keys<<<grid_for((h->n + kKeyPPT - 1) / kKeyPPT, 256), 256, 0, as_stream(stream)>>>(px, py, pz, h->n,
+                                                                                              make_cell_key_k(grid), keys);
   return check_launch("soax_cell_keys");
 }
 
