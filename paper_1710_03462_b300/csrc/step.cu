@@ -142,7 +142,7 @@ struct AosArgs {
 };
 
 template <bool ACC>
-__device__ __forceinline__ void step_aos_loop(const AosArgs& a, const StepC& kc, const TrigUnscaled& tg) {
+__device__ __forceinline__ void step_aos_loop(const AosArgs& a, const StepC& kc, const TrigScaled& tg) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     char* r = a.rec + i * a.R;
     const double* pp = reinterpret_cast<const double*>(r + a.pos_off);
@@ -163,15 +163,38 @@ __device__ __forceinline__ void step_aos_loop(const AosArgs& a, const StepC& kc,
   }
 }
 
-__global__ void __launch_bounds__(256) k_step_aos(AosArgs a, FlowK f) {
-  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
-  load_trig_table(s_tab);
+// The same arithmetic and tables as k_step_soa (the amplitude-scaled tables in 96 KB of
+// dynamic shared memory, two 512-thread blocks per SM), so that the SoA-AoS comparison
+// differs in the memory layout alone.
+constexpr int kAosBlock = 512;
+
+__global__ void __launch_bounds__(kAosBlock, 2) k_step_aos(AosArgs a, FlowK f) {
+  extern __shared__ float4 s_tab3[];
+  load_scaled_trig_tables(s_tab3, ff_from2(a.e.Af), ff_from2(a.e.Bf), ff_from2(a.e.Cf));
   const StepC kc = make_stepc(a.e, f);
-  const TrigUnscaled tg = trig_unscaled(s_tab, a.e);
+  const TrigScaled tg{s_tab3};
   if (a.acc_off >= 0)
     step_aos_loop<true>(a, kc, tg);
   else
     step_aos_loop<false>(a, kc, tg);
+}
+
+static int prepare_aos_kernel() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return cuda_fail(cudaGetLastError(), "soax_step_aos: device");
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return SOAX_OK;
+  cudaError_t err = cudaFuncSetAttribute((const void*)k_step_aos, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kScaledTrigBytes);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute((const void*)k_step_aos, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+  if (err != cudaSuccess) return cuda_fail(err, "soax_step_aos: kernel attributes");
+  done[dev] = true;
+  return SOAX_OK;
 }
 
 }  // namespace soax
@@ -217,10 +240,11 @@ extern "C" int soax_step_aos(soax_t h, void* aos_dev, const soax_flow* fl, int32
   a.tau_off = fl->tau_field >= 0 ? h->offsets[fl->tau_field] : -1;
   a.n = h->n;
   a.e = e;
-  const int grid = persistent_grid((const void*)k_step_aos, 256, 0, grid_for(h->n, 256));
+  if (int r = prepare_aos_kernel()) return r;
+  const int grid = persistent_grid((const void*)k_step_aos, kAosBlock, kScaledTrigBytes, grid_for(h->n, kAosBlock));
   // One pass over the records per step, like soax_step.
   for (int k = 0; k < nsteps; ++k) {
-    k_step_aos<<<grid, 256, 0, as_stream(stream)>>>(a, f);
+    k_step_aos<<<grid, kAosBlock, kScaledTrigBytes, as_stream(stream)>>>(a, f);
     if (int r = check_launch("soax_step_aos")) return r;
   }
   return SOAX_OK;
