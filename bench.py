@@ -74,8 +74,11 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="soax", choices=["soax", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
-    ap.add_argument("--only", choices=["euler"], help="run only this secondary row (profiling)")
-    ap.add_argument("--n", type=int, default=WL["n"], help=argparse.SUPPRESS)
+    ap.add_argument("--only", choices=["euler", "adjoint", "batched", "aos"],
+                    help="run only this secondary row (profiling captures)")
+    ap.add_argument("--n", type=int, default=None, help="particles (default: the row's workload)")
+    ap.add_argument("--nens", type=int, default=None, help="--only batched: the first NENS ensembles")
+    ap.add_argument("--fixed-tune", action="store_true", help="--only batched: a fixed launch shape, no autotuning")
     return ap.parse_args(argv)
 
 
@@ -341,11 +344,8 @@ def run_soax(args):
             dist.destroy_process_group()
         return 0
     fused_s = statistics.mean(fused_ms) / 1e3
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_inst = sms * SMSP_PER_SM * 32 * MAX_SM_MHZ * 1e6 / 1e12  # T thread-instructions/s
-    rec = ncu_record(STEP_KERNEL)
-    inst = float(rec["inst_per_particle_step"]) if rec and "inst_per_particle_step" in rec else None
-    achieved = inst * n * RK2_PER_STEP / fused_s / 1e12 if inst else None
+    roofline = alu_roofline(torch, dev, STEP_KERNEL, n * RK2_PER_STEP, fused_s)
+    roofline["hbm_GB/s"] = STEP_LAUNCH_BYTES * n / fused_s / 1e9
     sort_launches = 3 * 2  # (upsweep, scan, downsweep) x 2 passes; keys and permute-gather ride on the step
     line = {
         "metric": METRIC, "value": tot_units / max_el, "unit": "particle-steps/s", "n_gpus": world,
@@ -355,14 +355,7 @@ def run_soax(args):
                    "rk2_steps_per_step": RK2_PER_STEP, "grid": WL["grid"], "flow": "ABC A=B=C=1 tau=0.1 dt=1e-3",
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 ({n * 40 / 2**20:.0f} MiB of planes > 126 MiB)"},
-        "roofline": {"bound": "alu", "kernel": STEP_KERNEL, "achieved": achieved, "peak": peak_inst,
-                     "unit": "Tinst/s", "frac": achieved / peak_inst if achieved else None,
-                     "peak_kind": f"issue rate: 1 warp-instruction/clock per SM sub-partition x {SMSP_PER_SM} x "
-                                  f"{sms} SMs x 32 lanes at {MAX_SM_MHZ:.0f} MHz",
-                     "work_per_unit": inst, "work_unit": "thread-instructions per particle-step (ncu counter)",
-                     "units_per_launch": n * RK2_PER_STEP, "traffic": ncu_traffic(STEP_KERNEL),
-                     "hbm_GB/s": STEP_LAUNCH_BYTES * n / fused_s / 1e9,
-                     "launch_ms": statistics.mean(fused_ms)},
+        "roofline": roofline,
         "sort_ms": statistics.mean(sort_ms),
         "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d, "steps": e2e_steps,
@@ -418,38 +411,95 @@ def euler_replica(sx, torch, n, dev):
     return out
 
 
-def secondary_rows(sx, torch, p, d, dev):
-    rows = {}
+def issue_peak(torch, dev):
+    """Issue-rate peak in T thread-instructions/s and its description."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return (sms * SMSP_PER_SM * 32 * MAX_SM_MHZ * 1e6 / 1e12,
+            f"issue rate: 1 warp-instruction/clock per SM sub-partition x {SMSP_PER_SM} x {sms} SMs x 32 lanes "
+            f"at {MAX_SM_MHZ:.0f} MHz")
+
+
+def hbm_roofline(bytes_per_unit, units, seconds, kernel=None):
+    """Roofline entry of an HBM-bound launch: algorithmic bytes / time against the copy peak."""
+    peak, kind = measured_peaks()
+    achieved = bytes_per_unit * units / seconds / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": f"{kind} copy", "bytes_per_unit": bytes_per_unit,
+            "traffic": ncu_traffic(kernel) if kernel else None, "kernel": kernel}
+
+
+def alu_roofline(torch, dev, kernel, units, seconds):
+    """Roofline entry of an issue-bound launch: the thread-instructions per unit that ncu
+    counted for the current sources x units / time, against the issue-rate peak.  None
+    figures when no record matches the sources."""
+    peak, kind = issue_peak(torch, dev)
+    rec = ncu_record(kernel)
+    inst = float(rec["inst_per_particle_step"]) if rec and "inst_per_particle_step" in rec else None
+    achieved = inst * units / seconds / 1e12 if inst else None
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+            "frac": achieved / peak if achieved else None, "peak_kind": kind, "work_per_unit": inst,
+            "work_unit": "thread-instructions per particle-step (ncu counter)", "units_per_launch": units,
+            "traffic": ncu_traffic(kernel), "launch_ms": seconds * 1e3}
+
+
+def _events(torch, stream, fn, reps=1):
+    """Mean time in seconds of fn() over reps calls, with CUDA events on stream, after one
+    untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def row_one_pass(sx, torch, p, flow):
+    """The one-pass-per-step kernel (soax_step): HBM roofline at 72 bytes per particle-step."""
     n = p.n
-    flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
-    rows["euler_replica"] = euler_replica(sx, torch, n, dev)
-    # The one-pass-per-step kernel (soax_step): HBM roofline at 72 bytes per particle-step.
-    peak, peak_kind = measured_peaks()
     t1 = _time(torch, lambda: p.step(flow, 1), reps=10)
     tf = _time(torch, lambda: p.step_fused(flow, RK2_PER_STEP), reps=3)
-    rows["step_one_pass"] = {"kernel": "k_step_soa", "launch_ms": t1 * 1e3, "particle-steps/s": n / t1,
-                             "bound": "hbm", "achieved_GB/s": BYTES_PER_PARTICLE_STEP * n / t1 / 1e9, "peak_GB/s": peak,
-                             "frac": BYTES_PER_PARTICLE_STEP * n / t1 / 1e9 / peak, "peak_kind": f"{peak_kind} copy",
-                             "traffic": ncu_traffic("k_step_soa"),
-                             "fused_over_one_pass": t1 * RK2_PER_STEP / tf}
-    # AoS <-> SoA round trip (176 algorithmic bytes per particle) and the AoS step (96).
+    rl = hbm_roofline(BYTES_PER_PARTICLE_STEP, n, t1, "k_step_soa")
+    return {"kernel": "k_step_soa", "launch_ms": t1 * 1e3, "particle-steps/s": n / t1, "bound": "hbm",
+            "achieved_GB/s": rl["achieved"], "peak_GB/s": rl["peak"], "frac": rl["frac"],
+            "peak_kind": rl["peak_kind"], "traffic": rl["traffic"], "fused_over_one_pass": t1 * RK2_PER_STEP / tf,
+            "roofline": rl}
+
+
+def row_aos(sx, torch, p, flow):
+    """AoS <-> SoA round trip (176 algorithmic bytes per particle) and the AoS step (72
+    algorithmic bytes per particle-step, 96 moved in whole 48-B records)."""
+    n = p.n
     aos = p.to_aos()
     t_rt = _time(torch, lambda: (p.to_aos(aos), p.from_aos(aos)), reps=5)
-    rows["aos_soa_roundtrip"] = {"ms": t_rt * 1e3, "GB/s": 176 * n / t_rt / 1e9, "bytes_per_particle": 176}
+    rt = {"ms": t_rt * 1e3, "GB/s": 176 * n / t_rt / 1e9, "bytes_per_particle": 176,
+          "roofline": hbm_roofline(176, n, t_rt)}
     t_aos = _time(torch, lambda: p.step_aos(aos, flow, 1), reps=3)
     t_soa = _time(torch, lambda: p.step(flow, 1), reps=3)
-    rows["aos_step"] = {"particle-steps/s": n / t_aos, "algorithmic_GB/s": 72 * n / t_aos / 1e9,
-                        "record_GB/s": 96 * n / t_aos / 1e9, "soa_over_aos": t_aos / t_soa}
+    st = {"particle-steps/s": n / t_aos, "algorithmic_GB/s": 72 * n / t_aos / 1e9,
+          "record_GB/s": 96 * n / t_aos / 1e9, "soa_over_aos": t_aos / t_soa,
+          "roofline": hbm_roofline(72, n, t_aos, "k_step_aos")}
     del aos
     torch.cuda.empty_cache()
-    # Forward + adjoint (1M particles, K = 1000, checkpoint every 32) vs the plain step.
+    return rt, st
+
+
+def row_adjoint(sx, torch, dev, n=None):
+    """Forward (checkpoints every 32 steps) + adjoint of the 1M-particle K = 1000 problem,
+    against the plain step; each launch timed on its own and set against the issue rate
+    with the instructions per particle-step ncu counted (k_adj_forward: one forward step
+    with its checkpoint traffic; k_adj_reverse: one recomputed step and its reverse)."""
     wa = soax_inputs.WORKLOADS["adjoint_n1M"]
-    da = soax_inputs.basic_set(wa["n"], wa["seed"])
-    pa = sx.Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], wa["n"], device=dev, shadow=False)
+    n = wa["n"] if n is None else n
+    da = soax_inputs.basic_set(n, wa["seed"])
+    pa = sx.Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], n, device=dev, shadow=False)
     fa = sx.Flow(A=wa["A"], B=wa["B"], C=wa["C"], tau=wa["tau"], dt=wa["dt"])
     K, C = wa["K"], wa["ckpt_every"]
     wsa = pa.adjoint_workspace(K, C)
     xt = [torch.from_numpy(a).to(dev) for a in da["pos"]]
+    stream = torch.cuda.current_stream(dev)
 
     def reset():
         pa.load({"pos": da["pos"], "vel": da["vel"]})
@@ -459,42 +509,58 @@ def secondary_rows(sx, torch, p, d, dev):
     reset()
     t_plain_fused = _time(torch, lambda: pa.step_fused(fa, K))
     reset()
+    # Forward and adjoint timed apart (CUDA events on the launching stream), then together.
+    t_fwd = _events(torch, stream, lambda: pa.step_checkpointed(fa, K, C, wsa))
+    _, xb = pa.minimage_loss(xt, wsa)
+    t_rev = _events(torch, stream, lambda: pa.step_adjoint(fa, K, C, wsa, xb))
 
     def fwd_adj():
         pa.step_checkpointed(fa, K, C, wsa)
         _, xb = pa.minimage_loss(xt, wsa)
         pa.step_adjoint(fa, K, C, wsa, xb)
     t_fa = _time(torch, fwd_adj)
-    rows["fwd_adjoint"] = {"n": wa["n"], "K": K, "ckpt_every": C, "plain_ms": t_plain * 1e3,
-                           "plain_fused_ms": t_plain_fused * 1e3, "fwd_adj_ms": t_fa * 1e3,
-                           "ratio_vs_plain": t_fa / t_plain, "ratio_vs_plain_fused": t_fa / t_plain_fused}
+    out = {"n": n, "K": K, "ckpt_every": C, "plain_ms": t_plain * 1e3, "plain_fused_ms": t_plain_fused * 1e3,
+           "fwd_adj_ms": t_fa * 1e3, "fwd_ms": t_fwd * 1e3, "adj_ms": t_rev * 1e3,
+           "ratio_vs_plain": t_fa / t_plain, "ratio_vs_plain_fused": t_fa / t_plain_fused,
+           "roofline": {"k_adj_forward": alu_roofline(torch, dev, "k_adj_forward", n * K, t_fwd),
+                        "k_adj_reverse": alu_roofline(torch, dev, "k_adj_reverse", n * K, t_rev)}}
     del pa, wsa, xt
     torch.cuda.empty_cache()
-    # Batched: 512 uneven ensembles, a few steps, vs 512 plain launches per step.
+    return out
+
+
+def row_batched(sx, torch, dev, nens=None, fixed_tune=False):
+    """512 uneven ensembles (or the first nens of them): one persistent launch per step,
+    all 200 steps in one fused launch, and 512 plain launches per step in a CUDA graph.
+    fixed_tune: 2 particles per thread, 512 threads, 128-bit loads (the autotuner's usual
+    pick) instead of autotuning, so the launches are the same on every run (profiling)."""
     wb = soax_inputs.WORKLOADS["batched_512"]
     sizes, taus, abc = soax_inputs.ensembles(wb["nens"], wb["nmin"], wb["nmax"], wb["seed"])
+    nens = wb["nens"] if nens is None else nens
     parts, flows = [], []
-    for e, (ne, tau) in enumerate(zip(sizes, taus)):
-        q = sx.Particles(sx.BASIC_SCHEMA, int(ne), device=dev, shadow=False)
+    for e in range(nens):
+        ne, tau = int(sizes[e]), float(taus[e])
+        q = sx.Particles(sx.BASIC_SCHEMA, ne, device=dev, shadow=False)
         rng = np.random.default_rng(1000 + e)
-        pos = np.minimum(rng.uniform(0.0, soax_inputs.TWO_PI, (3, int(ne))), np.nextafter(soax_inputs.TWO_PI, 0))
-        vel = rng.normal(0.0, 0.1, (3, int(ne))).astype(np.float32)
+        pos = np.minimum(rng.uniform(0.0, soax_inputs.TWO_PI, (3, ne)), np.nextafter(soax_inputs.TWO_PI, 0))
+        vel = rng.normal(0.0, 0.1, (3, ne)).astype(np.float32)
         q.load({"pos": list(pos), "vel": list(vel)})
         parts.append(q)
-        flows.append(sx.Flow(A=abc[e, 0], B=abc[e, 1], C=abc[e, 2], tau=float(tau), dt=wb["dt"]))
-    total = int(sizes.sum())
+        flows.append(sx.Flow(A=abc[e, 0], B=abc[e, 1], C=abc[e, 2], tau=tau, dt=wb["dt"]))
+    total = int(sizes[:nens].sum())
     nst = 5
+    stream = torch.cuda.current_stream(dev)
     # One persistent launch per step (autotuned), over nst steps.
-    tune = sx.autotune(parts, flows, nsteps_probe=1)
+    tune = sx.Tune(2, 512, 128, 0) if fixed_tune else sx.autotune(parts, flows, nsteps_probe=1)
     wsb = sx.step_batched(parts, flows, 1, tune)
     t_b = _time(torch, lambda: sx.step_batched(parts, flows, nst, tune, ws=wsb))
     # The workload's form: all its steps in ONE fused persistent launch (autotuned).
-    tf = sx.autotune(parts, flows, nsteps_probe=10, fuse=True)
+    tf = sx.Tune(2, 512, 128, 1) if fixed_tune else sx.autotune(parts, flows, nsteps_probe=10, fuse=True)
     wsf = sx.batched_workspace(parts)
     sx.step_batched(parts, flows, 1, tf, ws=wsf)
     kf = wb["steps"]
-    t_f = _time(torch, lambda: sx.step_batched(parts, flows, kf, tf, ws=wsf))
-    # Baseline: 512 separate plain launches per step, captured in one CUDA graph.
+    t_f = _events(torch, stream, lambda: sx.step_batched(parts, flows, kf, tf, ws=wsf))
+    # Baseline: separate plain launches per step, captured in one CUDA graph.
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
     g = torch.cuda.CUDAGraph()
@@ -504,24 +570,49 @@ def secondary_rows(sx, torch, p, d, dev):
                 q.step(f, 1, stream=s)
     torch.cuda.current_stream(dev).wait_stream(s)
     t_plain_b = _time(torch, lambda: [g.replay() for _ in range(nst)])
-    rows["batched"] = {"ensembles": len(parts), "particles": total,
-                       "persistent": {"steps": nst, "tune": tune.__dict__,
-                                      "particle-steps/s": total * nst / t_b},
-                       "fused": {"steps": kf, "launches": 1, "tune": tf.__dict__, "ms": t_f * 1e3,
-                                 "particle-steps/s": total * kf / t_f},
-                       "plain_512_launches": {"steps": nst, "particle-steps/s": total * nst / t_plain_b},
-                       "persistent_over_plain": t_plain_b / t_b,
-                       "fused_over_plain": (t_plain_b / nst) / (t_f / kf)}
+    out = {"ensembles": len(parts), "particles": total,
+           "persistent": {"steps": nst, "tune": tune.__dict__, "particle-steps/s": total * nst / t_b,
+                          "roofline": hbm_roofline(BYTES_PER_PARTICLE_STEP, total * nst, t_b, "k_step_batched")},
+           "fused": {"steps": kf, "launches": 1, "tune": tf.__dict__, "ms": t_f * 1e3,
+                     "particle-steps/s": total * kf / t_f,
+                     "roofline": alu_roofline(torch, dev, "k_step_batched_fused", total * kf, t_f)},
+           "plain_launches": {"launches_per_step": len(parts), "steps": nst,
+                              "particle-steps/s": total * nst / t_plain_b},
+           "persistent_over_plain": t_plain_b / t_b,
+           "fused_over_plain": (t_plain_b / nst) / (t_f / kf)}
     del parts, g
     torch.cuda.empty_cache()
+    return out
+
+
+def secondary_rows(sx, torch, p, d, dev):
+    n = p.n
+    flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
+    rows = {"euler_replica": euler_replica(sx, torch, n, dev), "step_one_pass": row_one_pass(sx, torch, p, flow)}
+    rows["aos_soa_roundtrip"], rows["aos_step"] = row_aos(sx, torch, p, flow)
+    rows["fwd_adjoint"] = row_adjoint(sx, torch, dev)
+    rows["batched"] = row_batched(sx, torch, dev)
     return rows
 
 
 def run_only(args):
+    """One secondary row on its own, at a chosen size (for profiling captures)."""
     import torch
     import paper_1710_03462_b300 as sx
     dev = torch.device("cuda", torch.cuda.current_device())
-    print(json.dumps({"only": args.only, "row": euler_replica(sx, torch, args.n, dev)}))
+    if args.only == "euler":
+        row = euler_replica(sx, torch, args.n or WL["n"], dev)
+    elif args.only == "adjoint":
+        row = row_adjoint(sx, torch, dev, args.n)
+    elif args.only == "batched":
+        row = row_batched(sx, torch, dev, args.nens, args.fixed_tune)
+    else:
+        n = args.n or WL["n"]
+        flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
+        p = sx.Particles(sx.BASIC_SCHEMA, n, device=dev)
+        p.load(soax_inputs.basic_set(n, WL["seed"]))
+        row = dict(zip(("aos_soa_roundtrip", "aos_step"), row_aos(sx, torch, p, flow)))
+    print(json.dumps({"only": args.only, "n": args.n, "nens": args.nens, "fixed_tune": args.fixed_tune, "row": row}))
     return 0
 
 
@@ -529,6 +620,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.only:
         return run_only(args)
+    if args.n is None:
+        args.n = WL["n"]
     if args.impl == "reference":
         return run_reference(args)
     return run_soax(args)

@@ -19,7 +19,7 @@
 
 namespace soax {
 
-constexpr int kAdjBlock = 128;      // the reverse
+constexpr int kAdjBlock = 256;      // the reverse (2 blocks per SM with the scaled tables)
 constexpr int kAdjFwdBlock = 512;   // the forward (2 blocks per SM with the scaled tables)
 constexpr int kLossBlock = 256;
 
@@ -36,7 +36,7 @@ struct AdjWs {
 static AdjWs adj_plan(int64_t n, int K, int C) {
   AdjWs w;
   w.state_bytes = a256((size_t)n * 24) + a256((size_t)n * 12);
-  w.nck = (K + C - 1) / C;
+  w.nck = (int)(((int64_t)K + C - 1) / C);
   const size_t nb_adj = (size_t)((n + kAdjBlock - 1) / kAdjBlock);
   const size_t nb_loss = (size_t)((n + kLossBlock - 1) / kLossBlock);
   w.off_partials = 0;
@@ -87,15 +87,15 @@ __global__ void __launch_bounds__(kAdjFwdBlock, 2) k_adj_forward(EnsArgs e, Flow
   const bool fast = fast_positions(k, tk);
   uint64_t T[3] = {to_turns(e.px[i]), to_turns(e.py[i]), to_turns(e.pz[i])};
   float v[3] = {e.vx[i], e.vy[i], e.vz[i]}, a[3] = {0.f, 0.f, 0.f};
-  for (int s = 0; s < K; ++s) {
-    if (s % C == 0) {
-      StateRef r = state_at(ckpt, sb, e.n, s / C);
-      for (int c = 0; c < 3; ++c) {
-        r.T[c][i] = T[c];
-        r.v[c][i] = v[c];
-      }
+  int seg = 0;
+  for (int64_t s0 = 0; s0 < K; s0 += C, ++seg) {
+    StateRef r = state_at(ckpt, sb, e.n, seg);
+    for (int c = 0; c < 3; ++c) {
+      r.T[c][i] = T[c];
+      r.v[c][i] = v[c];
     }
-    adj_step<ACC>(k, tk, tg, fast, T, v, a);
+    const int len = (K - s0 < C) ? (int)(K - s0) : C;
+    for (int j = 0; j < len; ++j) adj_step<ACC>(k, tk, tg, fast, T, v, a);
   }
   e.px[i] = turns_to_x(T[0]);
   e.py[i] = turns_to_x(T[1]);
@@ -135,19 +135,63 @@ __device__ __forceinline__ void block_reduce_fixed(double (&v)[NV], double* out)
     for (int k = 0; k < NV; ++k) out[k] = red[k][0];
 }
 
-__global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, TurnsK tk, int K, int C, int nck,
-                                                          char* ckpt, char* stack, size_t sb, AdjIO io,
-                                                          double* partials) {
-  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
-  load_trig_table(s_tab);
+// The recompute's step when some coordinate is beyond the shift series, and the
+// reverse's sines and cosines in that case: rare, and out of line, which keeps the
+// reverse kernel's code (recompute and reverse alternate within each block) small
+// enough for the instruction cache.
+template <class Trig>
+__device__ __noinline__ void recompute_step_far(const StepC& k, const TurnsK& tk, const Trig& tg, uint64_t* T,
+                                               float* v) {
+  uint64_t t[3] = {T[0], T[1], T[2]};
+  float w[3] = {v[0], v[1], v[2]}, a[3];
+  rk2_step_turns<false, false>(k, tk, tg, t, w, a);
+  for (int c = 0; c < 3; ++c) {
+    T[c] = t[c];
+    v[c] = w[c];
+  }
+}
+
+template <class Trig>
+__device__ __noinline__ void reverse_trig_far(const StepC& k, const TurnsK& tk, const Trig& tg, const uint64_t* T,
+                                             const float* v, ff* P0, ff* Q0, ff* P1, ff* Q1) {
+  const uint64_t t[3] = {T[0], T[1], T[2]};
+  const float w[3] = {v[0], v[1], v[2]};
+  ff a0[3], b0[3], a1[3], b1[3];
+  step_trig_turns<false>(k, tk, tg, t, w, a0, b0, a1, b1);
+  for (int c = 0; c < 3; ++c) {
+    P0[c] = a0[c];
+    Q0[c] = b0[c];
+    P1[c] = a1[c];
+    Q1[c] = b1[c];
+  }
+}
+
+// Amplitudes at least this large in magnitude take the reverse on the amplitude-scaled
+// tables (the parameter gradients come out multiplied by their amplitude and are divided
+// once per particle); a smaller or zero amplitude takes the plain table.
+constexpr double kScaledReverseMinAmp = 0x1p-20;
+
+// SCALED: the three amplitude-scaled tables (96 KB, the forward's: the recompute reads the
+// same entries); otherwise the plain table (32 KB), scaled per lookup in the recompute
+// (the same bits) and read unscaled by the reverse.
+template <bool SCALED>
+__global__ void __launch_bounds__(kAdjBlock, 2) k_adj_reverse(EnsArgs e, FlowK f, TurnsK tk, int K, int C, int nck,
+                                                             char* ckpt, char* stack, size_t sb, AdjIO io,
+                                                             double* partials) {
+  extern __shared__ float4 s_tab[];
+  if constexpr (SCALED)
+    load_scaled_trig_tables(s_tab, ff_from2(e.Af), ff_from2(e.Bf), ff_from2(e.Cf));
+  else
+    load_trig_table(s_tab);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double th[4] = {0.0, 0.0, 0.0, 0.0};
   if (i < e.n) {
     const StepC k = make_stepc(e, f, i);
-    // The plain table scaled per lookup gives the bits of the forward's scaled tables.
-    const TrigUnscaled tg = trig_unscaled(s_tab, e);
+    const TrigScaled tsc{s_tab};
+    const TrigUnscaled tun = trig_unscaled(s_tab, e);  // amp = (B, C, A)
+    const TrigPlain tpl{s_tab};
     const bool fast = fast_positions(k, tk);
-    ff xb[3], vb[3], tf[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    ff xb[3], vb[3], G[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int c = 0; c < 3; ++c) {
       xb[c] = d2ff(io.xbK[c][i]);
       vb[c] = io.vbK[0] ? d2ff(io.vbK[c][i]) : ff{0.f, 0.f};
@@ -168,7 +212,17 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, T
           st.T[c][i] = T[c];
           st.v[c][i] = v[c];
         }
-        adj_step<false>(k, tk, tg, fast, T, v, a);
+        if constexpr (SCALED) {
+          if (fast && near_shift(k, v))
+            rk2_step_turns<false, true>(k, tk, tsc, T, v, a);
+          else
+            recompute_step_far(k, tk, tsc, T, v);
+        } else {
+          if (fast && near_shift(k, v))
+            rk2_step_turns<false, true>(k, tk, tun, T, v, a);
+          else
+            recompute_step_far(k, tk, tun, T, v);
+        }
       }
       for (int j = len - 1; j >= 0; --j) {
         StateRef st = state_at(stack, sb, e.n, j);
@@ -176,14 +230,30 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_reverse(EnsArgs e, FlowK f, T
           T[c] = st.T[c][i];
           v[c] = st.v[c][i];
         }
-        rk2_reverse_turns(k, tk, s_tab, T, v, xb, vb, tf);
+        ff P0[3], Q0[3], P1[3], Q1[3];
+        if constexpr (SCALED) {
+          if (near_shift(k, v))
+            step_trig_turns<true>(k, tk, tsc, T, v, P0, Q0, P1, Q1);
+          else
+            reverse_trig_far(k, tk, tsc, T, v, P0, Q0, P1, Q1);
+        } else {
+          if (near_shift(k, v))
+            step_trig_turns<true>(k, tk, tpl, T, v, P0, Q0, P1, Q1);
+          else
+            reverse_trig_far(k, tk, tpl, T, v, P0, Q0, P1, Q1);
+        }
+        rk2_reverse_core<SCALED>(k, tun.amp, P0, Q0, P1, Q1, v, xb, vb, G);
       }
     }
     for (int c = 0; c < 3; ++c) {
       io.xb0[c][i] = ff2d(xb[c]);
       io.vb0[c][i] = ff2d(vb[c]);
     }
-    for (int c = 0; c < 4; ++c) th[c] = ff2d(tf[c]);
+    // SCALED: G[0..2] = A dL/dA, B dL/dB, C dL/dC.  dL/dtau = -s^2 dL/ds = -s^2 dt G[3].
+    th[0] = SCALED ? ff2d(G[0]) / e.A : ff2d(G[0]);
+    th[1] = SCALED ? ff2d(G[1]) / e.B : ff2d(G[1]);
+    th[2] = SCALED ? ff2d(G[2]) / e.C : ff2d(G[2]);
+    th[3] = -ff2d(ff_mul(ff_mul(k.s, k.s), k.dt)) * ff2d(G[3]);
   }
   block_reduce_fixed<4, kAdjBlock>(th, partials + 4 * (size_t)blockIdx.x);
 }
@@ -233,19 +303,20 @@ __global__ void __launch_bounds__(kLossBlock) k_minimage_loss(LossIO io, int64_t
 
 // Dynamic shared memory above 48 KB and the largest carveout for the forward, once per
 // device.
-static int prepare_adj_forward() {
+static int prepare_adj_kernels() {
   static std::mutex mu;
   static bool done[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-    return cuda_fail(cudaGetLastError(), "soax_step_checkpointed: device");
+    return cuda_fail(cudaGetLastError(), "soax adjoint: device");
   std::lock_guard<std::mutex> lk(mu);
   if (done[dev]) return SOAX_OK;
-  for (const void* fn : {(const void*)k_adj_forward<true>, (const void*)k_adj_forward<false>}) {
+  for (const void* fn : {(const void*)k_adj_forward<true>, (const void*)k_adj_forward<false>,
+                         (const void*)k_adj_reverse<true>, (const void*)k_adj_reverse<false>}) {
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kScaledTrigBytes);
     if (err == cudaSuccess)
       err = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (err != cudaSuccess) return cuda_fail(err, "soax_step_checkpointed: kernel attributes");
+    if (err != cudaSuccess) return cuda_fail(err, "soax adjoint: kernel attributes");
   }
   done[dev] = true;
   return SOAX_OK;
@@ -290,7 +361,7 @@ extern "C" int soax_step_checkpointed(soax_t h, const soax_flow* fl, int32_t K, 
   AdjWs w;
   if (int r = adj_common(h, fl, K, ckpt_every, ws, ws_bytes, &e, &f, &w, "soax_step_checkpointed")) return r;
   if (h->n == 0 || K == 0) return SOAX_OK;
-  if (int r = prepare_adj_forward()) return r;
+  if (int r = prepare_adj_kernels()) return r;
   const auto kern = e.ax ? k_adj_forward<true> : k_adj_forward<false>;
   kern<<<grid_for(h->n, kAdjFwdBlock), kAdjFwdBlock, kScaledTrigBytes, as_stream(stream)>>>(
       e, f, make_turns_k(fl->dt, amplitude_bound(fl)), K, ckpt_every, static_cast<char*>(ws) + w.off_ckpt,
@@ -325,7 +396,12 @@ extern "C" int soax_step_adjoint(soax_t h, const soax_flow* fl, int32_t K, int32
   char* base = static_cast<char*>(ws);
   double* partials = reinterpret_cast<double*>(base + w.off_partials);
   const int nb = grid_for(h->n, kAdjBlock);
-  k_adj_reverse<<<nb, kAdjBlock, 0, s>>>(e, f, make_turns_k(fl->dt, amplitude_bound(fl)), K, ckpt_every, w.nck,
+  if (int r = prepare_adj_kernels()) return r;
+  const bool scaled = std::fabs(fl->A) >= kScaledReverseMinAmp && std::fabs(fl->B) >= kScaledReverseMinAmp &&
+                      std::fabs(fl->C) >= kScaledReverseMinAmp;
+  const auto rev = scaled ? k_adj_reverse<true> : k_adj_reverse<false>;
+  const size_t smem = scaled ? (size_t)kScaledTrigBytes : SOAX_TRIG_TABLE_SIZE * sizeof(float4);
+  rev<<<nb, kAdjBlock, smem, s>>>(e, f, make_turns_k(fl->dt, amplitude_bound(fl)), K, ckpt_every, w.nck,
                                         base + w.off_ckpt, base + w.off_stack, w.state_bytes, io, partials);
   if (int r = check_launch("soax_step_adjoint")) return r;
   k_reduce_partials<<<1, 256, 0, s>>>(partials, nb, 4, 1.0, grad);

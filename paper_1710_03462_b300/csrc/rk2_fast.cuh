@@ -124,7 +124,6 @@ __device__ __forceinline__ double f2d_exact(float f) {
 
 // Per-particle constants of the step, as float pairs.
 struct StepC {
-  ff A, B, C;    // flow amplitudes (the reverse pass; the forward step reads them from its table)
   ff dt, hdt;    // dt and dt/2
   ff s;          // 1/tau
   ff hs, ds, gh; // (dt/2)/tau, dt/tau and 1 - (dt/2)/tau (set_inv_tau)
@@ -200,6 +199,10 @@ struct TrigScaled {
   const float4* __restrict__ t;  // 3 x SOAX_TRIG_TABLE_SIZE entries: x, y, z
   __device__ __forceinline__ float4 operator()(int c, int k) const { return t[c * SOAX_TRIG_TABLE_SIZE + k]; }
 };
+struct TrigPlain {
+  const float4* __restrict__ t;  // the plain table: unscaled sin and cos for every coordinate
+  __device__ __forceinline__ float4 operator()(int, int k) const { return t[k]; }
+};
 struct TrigUnscaled {
   const float4* __restrict__ t;  // the plain table
   ff amp[3];                     // B, C, A
@@ -243,7 +246,8 @@ __device__ __forceinline__ void sincos_delta(ff sa, ff ca, ff d, ff& qs, ff& qc)
   qc = ff_sub(ff_mul(ca, cmd), ff_mul(sa, sd));
 }
 
-// sin and cos of a + d from those of a, |d| <= ~2e-3.
+// sin and cos of a + d from those of a, |d| <= ~2e-3 (or both times one amplitude: the
+// formulas are linear in sa, ca).
 __device__ __forceinline__ void sincos_shift(ff sa, ff ca, ff d, ff& s, ff& c) {
   // cos d - 1 and sin d by the series of series_terms (d^5/120 < 2e-16 relative, dropped)
   ff cmd, sd;
@@ -274,11 +278,20 @@ __device__ __forceinline__ double far_midpoint(double dt, double x, float v) {
   return xm < 0.0 ? xm + SOAX_TWO_PI : xm;
 }
 
-// u = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x) from the sines and cosines.
-__device__ __forceinline__ void abc_u(const StepC& k, const ff s[3], const ff c[3], ff u[3]) {
-  u[0] = ff_add(ff_mul(k.A, s[2]), ff_mul(k.C, c[1]));
-  u[1] = ff_add(ff_mul(k.B, s[0]), ff_mul(k.A, c[2]));
-  u[2] = ff_add(ff_mul(k.C, s[1]), ff_mul(k.B, c[0]));
+// u = (A sin z + C cos y, B sin x + A cos z, C sin y + B cos x).  SCALED: from the
+// amplitude-scaled sines and cosines P_c = a_c sin x_c, Q_c = a_c cos x_c (a = (B, C, A));
+// otherwise P, Q are sin and cos and amp = (B, C, A) multiplies them in.
+template <bool SCALED>
+__device__ __forceinline__ void abc_u(const ff amp[3], const ff P[3], const ff Q[3], ff u[3]) {
+  if constexpr (SCALED) {
+    u[0] = ff_add(P[2], Q[1]);
+    u[1] = ff_add(P[0], Q[2]);
+    u[2] = ff_add(P[1], Q[0]);
+  } else {
+    u[0] = ff_add(ff_mul(amp[2], P[2]), ff_mul(amp[1], Q[1]));
+    u[1] = ff_add(ff_mul(amp[0], P[0]), ff_mul(amp[2], Q[2]));
+    u[2] = ff_add(ff_mul(amp[1], P[1]), ff_mul(amp[0], Q[0]));
+  }
 }
 
 // One step: x (binary64 position, in/out), v (f32 velocity, in/out), a2out (the last
@@ -360,67 +373,70 @@ __device__ __forceinline__ void rk2_step_fast(const StepC& k, const Trig& trig, 
   rk2_update<ACC>(k, u0, du, x, v, a2out);
 }
 
-// xb += J(x)^T ub and th[0..2] += (du/d(A, B, C))^T ub at the point whose sines and
-// cosines are s, c:  J = [[0, -C sin y, A cos z], [B cos x, 0, -A sin z],
-// [-B sin x, C cos y, 0]],  du/dA = (sin z, cos z, 0), du/dB = (0, sin x, cos x),
-// du/dC = (cos y, 0, sin y).
-__device__ __forceinline__ void abc_vjp(const StepC& k, const ff s[3], const ff c[3], const ff ub[3], ff xb[3],
-                                        ff th[4]) {
-  const ff gA = ff_add(ff_mul(s[2], ub[0]), ff_mul(c[2], ub[1]));  // du/dA . ub
-  const ff gB = ff_add(ff_mul(s[0], ub[1]), ff_mul(c[0], ub[2]));
-  const ff gC = ff_add(ff_mul(c[1], ub[0]), ff_mul(s[1], ub[2]));
-  th[0] = ff_add(th[0], gA);
-  th[1] = ff_add(th[1], gB);
-  th[2] = ff_add(th[2], gC);
-  xb[0] = ff_add(xb[0], ff_mul(k.B, ff_sub(ff_mul(c[0], ub[1]), ff_mul(s[0], ub[2]))));
-  xb[1] = ff_add(xb[1], ff_mul(k.C, ff_sub(ff_mul(c[1], ub[2]), ff_mul(s[1], ub[0]))));
-  xb[2] = ff_add(xb[2], ff_mul(k.A, ff_sub(ff_mul(c[2], ub[0]), ff_mul(s[2], ub[1]))));
+// xb += J(x)^T ub and G[0..2] += (w du/dA, w du/dB, w du/dC)^T ub at the point whose
+// sines and cosines are P, Q.  SCALED: P_c = a_c sin x_c, Q_c = a_c cos x_c (a = (B, C, A))
+// and the weights w are the amplitudes (A, B, C); otherwise P, Q are sin and cos, w = 1
+// and amp = (B, C, A) multiplies each column of J.  In the scaled form
+// J = [[0, -P_y, Q_z], [Q_x, 0, -P_z], [-P_x, Q_y, 0]], A du/dA = (P_z, Q_z, 0),
+// B du/dB = (0, P_x, Q_x), C du/dC = (Q_y, 0, P_y): each coordinate's four products serve
+// its column of J and its amplitude's gradient.
+template <bool SCALED>
+__device__ __forceinline__ void abc_vjp(const ff amp[3], const ff P[3], const ff Q[3], const ff ub[3], ff xb[3],
+                                        ff G[4]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    // coordinate c enters u_{c+1} as a sine (P) and u_{c+2} as a cosine (Q), indices mod 3
+    const int p = c == 2 ? 0 : c + 1, q = c == 0 ? 2 : c - 1;
+    ff col = ff_sub(ff_mul(Q[c], ub[p]), ff_mul(P[c], ub[q]));
+    if constexpr (!SCALED) col = ff_mul(amp[c], col);
+    xb[c] = ff_add(xb[c], col);
+    // the amplitude of coordinate c: x -> B (G[1]), y -> C (G[2]), z -> A (G[0])
+    const int g = c == 2 ? 0 : c + 1;
+    G[g] = ff_add(G[g], ff_add(ff_mul(P[c], ub[p]), ff_mul(Q[c], ub[q])));
+  }
 }
 
 // Reverse of one step: given the adjoints (xb, vb) of (x', v'), overwrite them with the
-// adjoints of (x, v) and accumulate d/d(A, B, C, tau) into th.  (x, v) is the state
-// before the step, given by v and the sines and cosines of x (s0, c0) and of
-// xm = x + (dt/2) v (s1, c1), unscaled.  The f32 rounding of v' and the periodic wrap are differentiated as
-// the identity.  Reverse-mode differentiation of rk2_step_fast's statements, last first:
+// adjoints of (x, v), and accumulate into G the parameter gradients G[0..2] (w dL/dA,
+// w dL/dB, w dL/dC with the weights of abc_vjp) and the sum G[3] = S with dL/ds = dt S
+// (s = 1/tau); the caller finishes them once per particle.  (x, v) is the state before the
+// step, given by v and the sines and cosines at x (P0, Q0) and at xm = x + (dt/2) v
+// (P1, Q1), amplitude-scaled when SCALED.  The f32 rounding of v' and the periodic wrap are
+// differentiated as the identity.  With hs = (dt/2) s, ds = dt s, d0 = u(x) - v,
+// d1 = u(xm) - vm, the step's statements in reverse order:
 //   x' = x + dt vm:       xb += xb',  vmb = dt xb'
-//   v' = v + dt a2:       vb += vb',  a2b = dt vb'
-//   a2 = (u(xm) - vm) s:  u1b = s a2b,  vmb -= s a2b,  sb += a2b . (u1 - vm)
-//   u1 = u(xm):           xmb = J(xm)^T u1b,  thb += (du/dtheta)(xm)^T u1b
-//   vm = v + dt/2 a1:     vb += vmb,  a1b = dt/2 vmb
-//   xm = x + dt/2 v:      xb += xmb,  vb += dt/2 xmb
-//   a1 = (u(x) - v) s:    u0b = s a1b,  vb -= s a1b,  sb += a1b . (u0 - v)
-//   u0 = u(x):            xb += J(x)^T u0b,  thb += (du/dtheta)(x)^T u0b
-//   s = 1/tau:            taub = -s^2 sb
-__device__ __forceinline__ void rk2_reverse_core(const StepC& k, const ff s0[3], const ff c0[3], const ff s1[3],
-                                                 const ff c1[3], const float v[3], ff xb[3], ff vb[3], ff th[4]) {
+//   v' = v + ds d1:       vb += vb',  u1b = ds vb',  vmb -= ds vb',  S += vb' . d1
+//   u1 = u(xm):           xmb = J(xm)^T u1b,  G += (w du/dtheta)(xm)^T u1b
+//   vm = v + hs d0:       vb += vmb,  u0b = hs vmb,  vb -= hs vmb,  S += vmb . d0 / 2
+//   xm = x + (dt/2) v:    xb += xmb,  vb += (dt/2) xmb
+//   u0 = u(x):            xb += J(x)^T u0b,  G += (w du/dtheta)(x)^T u0b
+template <bool SCALED>
+__device__ __forceinline__ void rk2_reverse_core(const StepC& k, const ff amp[3], const ff P0[3], const ff Q0[3],
+                                                 const ff P1[3], const ff Q1[3], const float v[3], ff xb[3], ff vb[3],
+                                                 ff G[4]) {
   ff u0[3], u1[3];
-  abc_u(k, s0, c0, u0);
-  abc_u(k, s1, c1, u1);
-  ff d0[3], d1[3], u1b[3], vmb[3], xmb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  ff sb = {0.f, 0.f};
+  abc_u<SCALED>(amp, P0, Q0, u0);
+  abc_u<SCALED>(amp, P1, Q1, u1);
+  ff d0[3], u1b[3], vmb[3], xmb[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    d0[c] = ff_add_f(u0[c], -v[c]);  // u0 - v
-    const ff a1 = ff_mul(d0[c], k.s);
-    const ff vm = ff_add_f(ff_mul(k.hdt, a1), v[c]);
-    d1[c] = ff_sub(u1[c], vm);  // u1 - vm
-    const ff a2b = ff_mul(k.dt, vb[c]);
-    u1b[c] = ff_mul(k.s, a2b);
+    d0[c] = ff_add_f(u0[c], -v[c]);
+    const ff vm = ff_add_f(ff_mul(k.hs, d0[c]), v[c]);
+    const ff d1 = ff_sub(u1[c], vm);
+    u1b[c] = ff_mul(k.ds, vb[c]);
     vmb[c] = ff_sub(ff_mul(k.dt, xb[c]), u1b[c]);
-    sb = ff_add(sb, ff_mul(a2b, d1[c]));
+    G[3] = ff_add(G[3], ff_mul(vb[c], d1));
   }
-  abc_vjp(k, s1, c1, u1b, xmb, th);
+  abc_vjp<SCALED>(amp, P1, Q1, u1b, xmb, G);
   ff u0b[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const ff a1b = ff_mul(k.hdt, vmb[c]);
-    u0b[c] = ff_mul(k.s, a1b);
+    u0b[c] = ff_mul(k.hs, vmb[c]);
     vb[c] = ff_sub(ff_add(vb[c], ff_add(vmb[c], ff_mul(k.hdt, xmb[c]))), u0b[c]);
     xb[c] = ff_add(xb[c], xmb[c]);
-    sb = ff_add(sb, ff_mul(a1b, d0[c]));
+    G[3] = ff_add(G[3], ff_mul(ff{__fmul_rn(0.5f, vmb[c].h), __fmul_rn(0.5f, vmb[c].l)}, d0[c]));
   }
-  abc_vjp(k, s0, c0, u0b, xb, th);
-  th[3] = ff_sub(th[3], ff_mul(ff_mul(k.s, k.s), sb));
+  abc_vjp<SCALED>(amp, P0, Q0, u0b, xb, G);
 }
 
 static __device__ const float4 kTrigTable[SOAX_TRIG_TABLE_SIZE] = {SOAX_TRIG_TABLE_ENTRIES};

@@ -144,34 +144,26 @@ __device__ __forceinline__ void rk2_step_turns(const StepC& k, const TurnsK& tk,
   v[2] = vn[2];
 }
 
-// sin and cos (unscaled, from the plain table) of the three coordinates of the position T
-// (s0, c0) and of the midpoint T + (dt/2) v (s1, c1): the shift series, or the table at
-// the midpoint for a long shift, as in rk2_step_turns.
-__device__ __forceinline__ void step_trig_turns(const StepC& k, const TurnsK& tk, const float4* __restrict__ tab,
-                                                const uint64_t T[3], const float v[3], ff s0[3], ff c0[3], ff s1[3],
-                                                ff c1[3]) {
+// The amplitude-scaled sines and cosines of the three coordinates of the position T
+// (P0, Q0) and of the midpoint T + (dt/2) v (P1, Q1): the shift series, or the table at
+// the midpoint for a long shift, chosen per coordinate as in rk2_step_turns (NEAR: the
+// caller has checked near_shift).
+template <bool NEAR, class Trig>
+__device__ __forceinline__ void step_trig_turns(const StepC& k, const TurnsK& tk, const Trig& trig, const uint64_t T[3],
+                                                const float v[3], ff P0[3], ff Q0[3], ff P1[3], ff Q1[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     int idx;
     ff r;
     turns_angle(T[c], idx, r);
-    sincos_tab(tab[idx], r, s0[c], c0[c]);
-    if (fabsf(v[c]) <= k.vnear) {
-      sincos_shift(s0[c], c0[c], ff_mul_f(k.hdt, v[c]), s1[c], c1[c]);
+    sincos_tab(trig(c, idx), r, P0[c], Q0[c]);
+    if (NEAR || fabsf(v[c]) <= k.vnear) {
+      sincos_shift(P0[c], Q0[c], ff_mul_f(k.hdt, v[c]), P1[c], Q1[c]);
     } else {
       turns_angle(turns_add(T[c], ff_mul_f(tk.hdtT, v[c])), idx, r);
-      sincos_tab(tab[idx], r, s1[c], c1[c]);
+      sincos_tab(trig(c, idx), r, P1[c], Q1[c]);
     }
   }
-}
-
-// Reverse of one step from the state (T, v) before it (rk2_reverse_core).
-__device__ __forceinline__ void rk2_reverse_turns(const StepC& k, const TurnsK& tk, const float4* __restrict__ tab,
-                                                  const uint64_t T[3], const float v[3], ff xb[3], ff vb[3],
-                                                  ff th[4]) {
-  ff s0[3], c0[3], s1[3], c1[3];
-  step_trig_turns(k, tk, tab, T, v, s0, c0, s1, c1);
-  rk2_reverse_core(k, s0, c0, s1, c1, v, xb, vb, th);
 }
 
 }  // namespace soax

@@ -41,9 +41,6 @@ __device__ __forceinline__ ff particle_inv_tau(const EnsArgs& e, int64_t i) {
 // tau also the ones that depend on it.
 __device__ __forceinline__ StepC make_stepc(const EnsArgs& e, const FlowK& f) {
   StepC c;
-  c.A = ff_from2(e.Af);
-  c.B = ff_from2(e.Bf);
-  c.C = ff_from2(e.Cf);
   c.dt = ff_from2(f.dtf);
   c.hdt = ff_from2(f.hdtf);
   c.dt_d = f.dt;

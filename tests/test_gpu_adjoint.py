@@ -76,6 +76,44 @@ def test_adjoint_vs_oracle(n, K, C):
         assert np.max(np.abs(vb[c] - ovb[c])[ok]) <= 1e-9 * scale
 
 
+@pytest.mark.parametrize("th", [[0.0, 0.95, 1.05, 0.12], [1.0, 1e-7, 1.05, 0.12], [-1.0, 0.95, -1.05, 0.2]])
+def test_adjoint_vs_oracle_amplitude_forms(th):
+    """The reverse runs on amplitude-scaled tables when every |amplitude| >= 2^-20 (the
+    gradients come out times their amplitude and are divided once per particle) and on the
+    plain table otherwise: a zero and a tiny amplitude (plain table; dL/dA is still
+    defined at A = 0) and negative ones (scaled) against the oracle."""
+    n, K, C = 1000, 70, 32
+    d = soax_inputs.basic_set(n, 7)
+    xt = _target(d, K)
+    p, loss, xb, vb, g = _gpu_adjoint(d, xt, K, C, th)
+    ol, oxb, ovb, og = oracle.adjoint(d["pos"], d["vel"], xt, *th, 1e-3, K, f32v=True)
+    ok = ~_diverged(p, d, th, K)
+    assert abs(loss - ol) <= 1e-9 * abs(ol)
+    assert np.all(np.isfinite(g))
+    assert np.allclose(g, og, rtol=1e-8, atol=0), (g, og)
+    for c in range(3):
+        scale = max(np.abs(oxb[c]).max(), 1e-300)
+        assert np.max(np.abs(xb[c] - oxb[c])[ok]) <= 1e-9 * scale
+        scale = max(np.abs(ovb[c]).max(), 1e-300)
+        assert np.max(np.abs(vb[c] - ovb[c])[ok]) <= 1e-9 * scale
+
+
+def test_adjoint_scaled_and_plain_forms_agree():
+    """An amplitude just at 2^-20 (scaled tables) and the next binary64 below it (plain
+    table) differ by one ulp of the amplitude: the two reverse forms give the same
+    gradients to float-pair accuracy."""
+    n, K, C = 2000, 40, 16
+    d = soax_inputs.basic_set(n, 3)
+    xt = _target(d, K)
+    a = 2.0 ** -20
+    _, _, xb1, vb1, g1 = _gpu_adjoint(d, xt, K, C, [1.0, a, 1.05, 0.12])
+    _, _, xb2, vb2, g2 = _gpu_adjoint(d, xt, K, C, [1.0, np.nextafter(a, 0.0), 1.05, 0.12])
+    assert np.allclose(g1, g2, rtol=1e-9, atol=0), (g1, g2)
+    for c in range(3):
+        assert np.max(np.abs(xb1[c] - xb2[c])) <= 1e-10 * np.abs(xb1[c]).max()
+        assert np.max(np.abs(vb1[c] - vb2[c])) <= 1e-10 * np.abs(vb1[c]).max()
+
+
 def test_checkpointed_forward_equals_fused_step():
     """The checkpointed forward is soax_step_fused's arithmetic: the same bits as one fused
     launch of K steps."""
