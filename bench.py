@@ -337,6 +337,7 @@ def run_soax(args):
     torch.cuda.synchronize(dev)
     e2e_el = time.perf_counter() - t0
     e2e_units, e2e_max = aggregate(n * RK2_PER_STEP * e2e_steps, e2e_el, dev)
+    link = host_link(torch, dev, host, p, planes, s_up, s_dn)
 
     rows = {} if args.no_rows else secondary_rows(sx, torch, p, d, dev)
     if rank != 0:
@@ -360,7 +361,16 @@ def run_soax(args):
         "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d, "steps": e2e_steps,
                 "copies": "per plane, uploads and downloads on two streams (step k's download of a plane "
-                          "overlaps step k+1's uploads of the others)"},
+                          "overlaps step k+1's uploads of the others)",
+                "link": link,
+                # Each step's state must come back before the next step's can go up, and the
+                # step needs all of it: per step at least the step's device time plus one
+                # round trip at the two directions' combined rate; the first upload and the
+                # last download of the run are not overlapped at all.
+                "floor": n * RK2_PER_STEP * e2e_steps / (
+                    e2e_steps * (max_el / args.steps + 2 * h2d / (link["both_GB/s"] * 1e9))
+                    + h2d / (link["h2d_GB/s"] * 1e9) + h2d / (link["d2h_GB/s"] * 1e9)
+                    - 2 * h2d / (link["both_GB/s"] * 1e9))},
         "gpu_launches": args.steps * (1 + sort_launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu_baseline(n) if world == 1 or rank == 0 else None,
@@ -370,6 +380,43 @@ def run_soax(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def host_link(torch, dev, host, p, planes, s_up, s_dn):
+    """The host link's rates for the e2e state (pinned memory, one copy per plane): all
+    planes up alone, down alone, and both directions at once (GB/s, total bytes moved).
+    The e2e loop overlaps one step's downloads with the next step's uploads of other
+    planes, so "both" uploads the planes while downloading the same number of bytes from
+    a separate device buffer into a separate pinned buffer."""
+    nbytes = sum(t.numel() * t.element_size() for v in host.values() for t in v)
+    dev_scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    host_scratch = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+
+    def up():
+        with torch.cuda.stream(s_up):
+            for k, c in planes:
+                p.field(k)[c].copy_(host[k][c], non_blocking=True)
+
+    def down():
+        with torch.cuda.stream(s_dn):
+            for k, c in planes:
+                host[k][c].copy_(p.field(k)[c], non_blocking=True)
+
+    def down_scratch():
+        with torch.cuda.stream(s_dn):
+            host_scratch.copy_(dev_scratch, non_blocking=True)
+
+    out = {}
+    for name, fn, moved in (("h2d_GB/s", up, nbytes), ("d2h_GB/s", down, nbytes),
+                            ("both_GB/s", lambda: (up(), down_scratch()), 2 * nbytes)):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        out[name] = moved * 3 / (time.perf_counter() - t0) / 1e9
+    return out
 
 
 def _time(torch, fn, reps=1):
