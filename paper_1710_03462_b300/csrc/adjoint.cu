@@ -24,6 +24,7 @@ constexpr int kAdjFwdBlock = 512;   // the forward (2 blocks per SM with the sca
 constexpr int kLossBlock = 256;
 
 TurnsK make_turns_k(double dt, double umax);
+TurnsK make_turns_k(const soax_flow* fl, const FlowK& f, int nsteps);
 double amplitude_bound(const soax_flow* fl);
 
 __host__ __device__ static inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -75,6 +76,29 @@ __device__ __forceinline__ void adj_step(const StepC& k, const TurnsK& tk, const
     rk2_step_turns<ACC, false>(k, tk, tg, T, v, a);
 }
 
+// The forward's K steps from (T, v), writing the state before every C-th step as a
+// checkpoint.  SAFE: every step is known to be within the shift series (no check).
+template <bool ACC, bool SAFE, class Trig>
+__device__ __forceinline__ void forward_segments(const StepC& k, const TurnsK& tk, const Trig& tg, bool fast, int K,
+                                                 int C, char* ckpt, size_t sb, int64_t n, int64_t i, uint64_t T[3],
+                                                 float v[3], float a[3]) {
+  int seg = 0;
+  for (int64_t s0 = 0; s0 < K; s0 += C, ++seg) {
+    StateRef r = state_at(ckpt, sb, n, seg);
+    for (int c = 0; c < 3; ++c) {
+      r.T[c][i] = T[c];
+      r.v[c][i] = v[c];
+    }
+    const int len = (K - s0 < C) ? (int)(K - s0) : C;
+    for (int j = 0; j < len; ++j) {
+      if constexpr (SAFE)
+        rk2_step_turns<ACC, true>(k, tk, tg, T, v, a);
+      else
+        adj_step<ACC>(k, tk, tg, fast, T, v, a);
+    }
+  }
+}
+
 template <bool ACC>
 __global__ void __launch_bounds__(kAdjFwdBlock, 2) k_adj_forward(EnsArgs e, FlowK f, TurnsK tk, int K, int C,
                                                                   char* ckpt, size_t sb) {
@@ -87,16 +111,11 @@ __global__ void __launch_bounds__(kAdjFwdBlock, 2) k_adj_forward(EnsArgs e, Flow
   const bool fast = fast_positions(k, tk);
   uint64_t T[3] = {to_turns(e.px[i]), to_turns(e.py[i]), to_turns(e.pz[i])};
   float v[3] = {e.vx[i], e.vy[i], e.vz[i]}, a[3] = {0.f, 0.f, 0.f};
-  int seg = 0;
-  for (int64_t s0 = 0; s0 < K; s0 += C, ++seg) {
-    StateRef r = state_at(ckpt, sb, e.n, seg);
-    for (int c = 0; c < 3; ++c) {
-      r.T[c][i] = T[c];
-      r.v[c][i] = v[c];
-    }
-    const int len = (K - s0 < C) ? (int)(K - s0) : C;
-    for (int j = 0; j < len; ++j) adj_step<ACC>(k, tk, tg, fast, T, v, a);
-  }
+  // All K steps within the shift series (TurnsK::vsafe for K steps): no check per step.
+  if (fast && fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))) <= tk.vsafe)
+    forward_segments<ACC, true>(k, tk, tg, fast, K, C, ckpt, sb, e.n, i, T, v, a);
+  else
+    forward_segments<ACC, false>(k, tk, tg, fast, K, C, ckpt, sb, e.n, i, T, v, a);
   e.px[i] = turns_to_x(T[0]);
   e.py[i] = turns_to_x(T[1]);
   e.pz[i] = turns_to_x(T[2]);
@@ -364,7 +383,7 @@ extern "C" int soax_step_checkpointed(soax_t h, const soax_flow* fl, int32_t K, 
   if (int r = prepare_adj_kernels()) return r;
   const auto kern = e.ax ? k_adj_forward<true> : k_adj_forward<false>;
   kern<<<grid_for(h->n, kAdjFwdBlock), kAdjFwdBlock, kScaledTrigBytes, as_stream(stream)>>>(
-      e, f, make_turns_k(fl->dt, amplitude_bound(fl)), K, ckpt_every, static_cast<char*>(ws) + w.off_ckpt,
+      e, f, make_turns_k(fl, f, K), K, ckpt_every, static_cast<char*>(ws) + w.off_ckpt,
       w.state_bytes);
   return check_launch("soax_step_checkpointed");
 }

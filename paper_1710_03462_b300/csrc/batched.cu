@@ -109,6 +109,19 @@ __device__ __forceinline__ void batched_fused_span(const EnsArgs& e, const StepC
   }
 }
 
+// TurnsK::vsafe for nsteps steps of ensemble e (its own h = dt/tau and amplitude bound),
+// as make_turns_k(fl, f, nsteps) forms it for one ensemble; -1 with tau per particle.
+__device__ __forceinline__ float ensemble_vsafe(const EnsArgs& e, const FlowK& f, int nsteps) {
+  if (e.tau_src) return -1.0f;
+  const float vnear = __fdiv_rn(0x1p-9f, f.hdtf.x);  // StepC::vnear
+  const double h = f.dt * e.inv_tau;
+  const double F = pow((1.0 + h * h) * (1.0 + 0x1p-23), (double)nsteps);
+  const double a = fabs(e.A), b = fabs(e.B), c = fabs(e.C);
+  const double um = fmax(a + c, fmax(b + a, c + b)) * (1.0 + 1e-6);
+  const double vs = (double)vnear / (1.001 * F);
+  return isfinite(vs) && vs >= um ? (float)vs : -1.0f;
+}
+
 template <int PPT, int MINB, int FORM>
 __global__ void __launch_bounds__(512, MINB) k_step_batched_fused(const PlanHeader* __restrict__ hdr,
                                                                   const EnsArgs* __restrict__ ens,
@@ -117,6 +130,7 @@ __global__ void __launch_bounds__(512, MINB) k_step_batched_fused(const PlanHead
                                                                   int* status) {
   extern __shared__ float4 s_tab3[];
   __shared__ EnsArgs s_e;  // the current ensemble's arguments (read, not held in registers)
+  __shared__ float s_vsafe;  // and its TurnsK::vsafe for this call
   const int64_t tile_parts = (int64_t)blockDim.x * PPT;
   if (!plan_ok(hdr, nens, ntiles, tile_parts, status)) return;
   int cur = -1;
@@ -128,7 +142,10 @@ __global__ void __launch_bounds__(512, MINB) k_step_batched_fused(const PlanHead
     }
     if (lo != cur) {  // uniform over the block, as t is
       __syncthreads();  // every thread is done with the previous ensemble's tables
-      if (threadIdx.x == 0) s_e = ens[lo];
+      if (threadIdx.x == 0) {
+        s_e = ens[lo];
+        s_vsafe = ensemble_vsafe(ens[lo], f, nsteps);
+      }
       load_scaled_trig_tables(s_tab3, ff_from2(ens[lo].Af), ff_from2(ens[lo].Bf), ff_from2(ens[lo].Cf));
       cur = lo;
     }
@@ -137,7 +154,9 @@ __global__ void __launch_bounds__(512, MINB) k_step_batched_fused(const PlanHead
     if (i0 < e.n) {
       const StepC kc = make_stepc(e, f);
       const TrigScaled tg{s_tab3};
-      batched_fused_span<FORM, FORM == 1 || FORM == 3, FORM == 2 || FORM == 3, PPT>(e, kc, tk, tg, i0, e.n - i0,
+      TurnsK tke = tk;
+      tke.vsafe = s_vsafe;
+      batched_fused_span<FORM, FORM == 1 || FORM == 3, FORM == 2 || FORM == 3, PPT>(e, kc, tke, tg, i0, e.n - i0,
                                                                                      nsteps);
     }
   }

@@ -23,6 +23,10 @@ namespace soax {
 struct TurnsK {
   ff dtT, hdtT;
   float umax;
+  // A particle whose speeds are all <= vsafe at the start of a call stays within the
+  // shift series (|v_c| <= vnear) for every step of it (set per launch from dt, tau and
+  // the number of steps by the host; -1: no such guarantee).
+  float vsafe;
 };
 
 // f (a displacement in units of 2^-32 turn, any magnitude) as 2^-64 turns modulo 2^64,

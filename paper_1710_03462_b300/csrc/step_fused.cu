@@ -56,12 +56,32 @@ TurnsK make_turns_k(double dt, double umax) {
   t.dtT = ff{a.x, a.y};
   t.hdtT = ff{b.x, b.y};
   t.umax = (float)(umax * (1.0 + 1e-6));
+  t.vsafe = -1.0f;
   return t;
 }
 
 double amplitude_bound(const soax_flow* fl) {
   const double a = std::fabs(fl->A), b = std::fabs(fl->B), c = std::fabs(fl->C);
   return std::fmax(a + c, std::fmax(b + a, c + b));
+}
+
+// The turns constants of a call of nsteps steps, with vsafe (TurnsK) when tau is uniform.
+// One step gives
+//   v' = v (1 - h + h^2/2) + h u(xm) - (h^2/2) u(x),   h = dt/tau,
+// so with |v_c| <= M and |u_c| <= umax <= M every component obeys |v'_c| <= M (1 + h^2)
+// (1 - h + h^2/2 >= 0 for every h), times 1 + 2^-23 for the f32 rounding of v'.  After
+// nsteps steps the speeds stay below M F, F = ((1 + h^2)(1 + 2^-23))^nsteps; with
+// M <= vsafe = vnear / (1.001 F) (the margin covers the float-pair errors of u) every step
+// is within the shift series.  -1 when umax itself exceeds that.
+TurnsK make_turns_k(const soax_flow* fl, const FlowK& f, int nsteps) {
+  TurnsK t = make_turns_k(fl->dt, amplitude_bound(fl));
+  if (fl->tau_field >= 0 || nsteps < 0) return t;  // per-particle tau: no launch-wide h
+  const float vnear = 0x1p-9f / f.hdtf.x;        // StepC::vnear, the same float division
+  const double h = f.dt / fl->tau;
+  const double F = std::pow((1.0 + h * h) * (1.0 + 0x1p-23), (double)nsteps);
+  const double vs = (double)vnear / (1.001 * F);
+  if (std::isfinite(vs) && vs >= (double)t.umax) t.vsafe = (float)vs;
+  return t;
 }
 
 static int step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t grid, uint32_t* keys, void* stream,
@@ -84,7 +104,7 @@ static int step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t gri
   const FusedKernel kern = fused_kernel(e.tau_src != nullptr, e.ax != nullptr);
   const int gsz = persistent_grid((const void*)kern, kFusedBlock, kScaledTrigBytes,
                                   grid_for((h->n + kFusedPPT - 1) / kFusedPPT, kFusedBlock));
-  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(e, f, make_turns_k(fl->dt, amplitude_bound(fl)), nsteps,
+  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(e, f, make_turns_k(fl, f, nsteps), nsteps,
                                                                    grid ? keys : nullptr, ck);
   return check_launch(who);
 }
@@ -165,7 +185,7 @@ static int permute_step_fused(soax_t h, const uint32_t* perm, const soax_flow* f
   if (int r = prepare_gather_kernels()) return r;
   const GatherKernel kern = gather_kernel(ein.tau_src != nullptr, ein.ax != nullptr);
   const int gsz = persistent_grid((const void*)kern, kFusedBlock, kScaledTrigBytes, grid_for(h->n, kFusedBlock));
-  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(ein, eout, g, f, make_turns_k(fl->dt, amplitude_bound(fl)), nsteps,
+  kern<<<gsz, kFusedBlock, kScaledTrigBytes, as_stream(stream)>>>(ein, eout, g, f, make_turns_k(fl, f, nsteps), nsteps,
                                                                   grid ? keys : nullptr, ck);
   if (int r = check_launch(who)) return r;
   h->current = dst;

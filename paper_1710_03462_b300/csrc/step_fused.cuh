@@ -69,7 +69,21 @@ __device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, c
     if constexpr (TAU) set_inv_tau(k, sj[j]);
     fast = fast && fast_positions(k, tk);
   }
-  for (int s = 0; s < nsteps; ++s) {
+  // Every step of the call stays within the shift series when every particle starts at
+  // speeds <= vsafe (TurnsK::vsafe): then no check per step (the same bits).
+  // (With tau per particle there is no launch-wide guarantee: vsafe is -1.)
+  bool safe = !TAU && fast;
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) safe = safe && fmaxf(fabsf(v[j][0]), fmaxf(fabsf(v[j][1]), fabsf(v[j][2]))) <= tk.vsafe;
+  if constexpr (!TAU) {
+    if (safe) {
+      for (int s = 0; s < nsteps; ++s) {
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) rk2_step_turns<ACC, true>(k, tk, trig, T[j], v[j], a[j]);
+      }
+    }
+  }
+  for (int s = 0; s < (safe ? 0 : nsteps); ++s) {
     bool near = fast;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) near = near && near_shift(k, v[j]);
@@ -211,11 +225,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused_gather(EnsArgs e
     StepC k = kc;
     if constexpr (TAU) set_inv_tau(k, particle_inv_tau<true>(ein, src));
     const bool fast = fast_positions(k, tk);
-    for (int s = 0; s < nsteps; ++s) {
-      if (fast && near_shift(k, v))
-        rk2_step_turns<ACC, true>(k, tk, tg, T, v, a);
-      else
-        rk2_step_turns<ACC, false>(k, tk, tg, T, v, a);
+    if (!TAU && fast && fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))) <= tk.vsafe) {
+      // Every step of this call stays within the shift series (TurnsK::vsafe): no check
+      // per step.  The same bits as the checked loop below.
+      for (int s = 0; s < nsteps; ++s) rk2_step_turns<ACC, true>(k, tk, tg, T, v, a);
+    } else {
+      for (int s = 0; s < nsteps; ++s) {
+        if (fast && near_shift(k, v))
+          rk2_step_turns<ACC, true>(k, tk, tg, T, v, a);
+        else
+          rk2_step_turns<ACC, false>(k, tk, tg, T, v, a);
+      }
     }
     const double x = turns_to_x(T[0]), y = turns_to_x(T[1]), z = turns_to_x(T[2]);
     eout.px[i] = x;
