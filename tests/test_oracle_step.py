@@ -8,7 +8,10 @@ box), each fixed by mathematics rather than by the oracle's own formula:
   * an independent 50-digit brute-force step on a few particles (mpmath);
   * the AoS and SoA variants are bit-equal;
   * per-particle tau from the mass field equals uniform tau when all masses are equal;
-  * the Euler step of Eq. 1 equals numpy's float32 x + dt*v.
+  * the Euler step of Eq. 1 equals numpy's float32 x + dt*v;
+  * speeds grow by at most (1 + h^2)(1 + 2^-23) per step past max(|v|, max |u|), and a
+    constructed particle reaches that factor (the bound the fused kernels rely on to skip
+    their per-step check).
 """
 import math
 
@@ -268,3 +271,39 @@ def test_remove_by_overwrite_with_last_pins():
     # Holes below n - k take the surviving tail particles in ascending order.
     out = oracle.remove([np.arange(10, dtype=np.int32)], np.array([2, 4, 7], np.uint32))[0]
     assert out.tolist() == [0, 1, 8, 3, 9, 5, 6]
+
+
+def test_speed_bound_per_step():
+    """The bound behind the fused kernels' check-free path (no check per step for a particle
+    whose starting speeds are below the launch's vsafe): one midpoint step is
+    v' = v(1 - h + h^2/2) + h u(xm) - (h^2/2) u(x) with h = dt/tau, and 1 - h + h^2/2 > 0,
+    so if |v_c| and every |u_c| are at most M then |v'_c| <= M (1 + h^2), times 1 + 2^-23
+    for the f32 rounding of v'.  Checked on the oracle's trajectories, per particle, for
+    small and large h, negative amplitudes, and speeds on both sides of the flow's
+    amplitude bound."""
+    rng = np.random.default_rng(11)
+    n, nsteps = 4000, 25
+    for A, B, C, tau, dt in ((1.0, 1.0, 1.0, 0.1, 1e-3), (1.5, -0.5, 1.3, 0.01, 1e-3),
+                             (-1.2, 1.1, 0.6, 0.2, 0.1), (1.0, 1.0, 1.0, 0.05, 0.05),
+                             (0.3, 2.0, -1.0, 1.0, 0.5)):
+        h = dt / tau
+        umax = max(abs(A) + abs(C), abs(B) + abs(A), abs(C) + abs(B))
+        pos = [rng.uniform(0.0, TWO_PI, n) for _ in range(3)]
+        vel = [(rng.standard_normal(n) * rng.choice([0.1, 1.0, 5.0], n)).astype(np.float32) for _ in range(3)]
+        M = np.maximum(np.max(np.abs(np.stack(vel)).astype(np.float64), axis=0), umax)
+        grow = (1.0 + h * h) * (1.0 + 2.0 ** -23)
+        for s in range(1, nsteps + 1):
+            oracle.step_soa(pos, vel, A, B, C, tau, dt, 1)
+            speed = np.max(np.abs(np.stack(vel)).astype(np.float64), axis=0)
+            assert np.all(speed <= M * grow ** s), (A, B, C, tau, dt, s)
+    # The growth factor is needed: with B = C = 0 (u = (A sin z, A cos z, 0)), v_x = A and a
+    # half-step shift of -pi in z from 3 pi/2, u_x(x) = -A and u_x(xm) = +A, so
+    # v'_x = A (1 - h + h^2/2) + h A + (h^2/2) A = A (1 + h^2) exactly in real arithmetic.
+    A, tau, dt = 2 * math.pi, 1.0, 1.0
+    h = dt / tau
+    pos = [np.array([0.5]), np.array([0.5]), np.array([1.5 * math.pi])]
+    vel = [np.array([A], np.float32), np.array([0.0], np.float32), np.array([-A], np.float32)]
+    M = max(float(np.abs(vel[0][0])), float(np.abs(vel[2][0])), A)
+    oracle.step_soa(pos, vel, A, 0.0, 0.0, tau, dt, 1)
+    vx = float(vel[0][0])
+    assert M * (1.0 + h * h) * (1.0 - 1e-6) < vx <= M * (1.0 + h * h) * (1.0 + 2.0 ** -23)
