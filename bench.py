@@ -306,8 +306,8 @@ def run_soax(args):
     units = n * RK2_PER_STEP * args.steps
     tot_units, max_el = aggregate(units, elapsed, dev)
 
-    # e2e through the public API with host buffers: the state goes up and comes back
-    # every bench step (pinned memory, one async copy per plane).  Uploads run on one copy
+    # e2e through the C ABI with host buffers: the state goes up and comes back every
+    # bench step (pinned memory, one soax_copy_plane per plane).  Uploads run on one copy
     # stream, downloads on another, so the link's two directions work at once: plane q's
     # upload for step k + 1 waits only for plane q's download of step k (the same host
     # buffer and device plane), and the step waits for all of its uploads.
@@ -320,20 +320,18 @@ def run_soax(args):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with torch.cuda.stream(s_up):
-            for k, c in planes:
-                if (k, c) in down:
-                    s_up.wait_event(down[(k, c)])
-                p.field(k)[c].copy_(host[k][c], non_blocking=True)
+        for k, c in planes:
+            if (k, c) in down:
+                s_up.wait_event(down[(k, c)])
+            p.copy_plane(k, c, host[k][c], True, stream=s_up)  # soax_copy_plane, host -> device
         stream.wait_stream(s_up)
         bench_step()
         s_dn.wait_stream(stream)
-        with torch.cuda.stream(s_dn):
-            for k, c in planes:
-                host[k][c].copy_(p.field(k)[c], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(s_dn)
-                down[(k, c)] = ev
+        for k, c in planes:
+            p.copy_plane(k, c, host[k][c], False, stream=s_dn)  # device -> host
+            ev = torch.cuda.Event()
+            ev.record(s_dn)
+            down[(k, c)] = ev
     torch.cuda.synchronize(dev)
     e2e_el = time.perf_counter() - t0
     e2e_units, e2e_max = aggregate(n * RK2_PER_STEP * e2e_steps, e2e_el, dev)
@@ -360,8 +358,8 @@ def run_soax(args):
         "sort_ms": statistics.mean(sort_ms),
         "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d, "steps": e2e_steps,
-                "copies": "per plane, uploads and downloads on two streams (step k's download of a plane "
-                          "overlaps step k+1's uploads of the others)",
+                "copies": "soax_copy_plane per plane, uploads and downloads on two streams (step k's "
+                          "download of a plane overlaps step k+1's uploads of the others)",
                 "link": link,
                 # Each step's state must come back before the next step's can go up, and the
                 # step needs all of it: per step at least the step's device time plus one
@@ -383,7 +381,7 @@ def run_soax(args):
 
 
 def host_link(torch, dev, host, p, planes, s_up, s_dn):
-    """The host link's rates for the e2e state (pinned memory, one copy per plane): all
+    """The host link's rates for the e2e state (pinned memory, one soax_copy_plane per plane): all
     planes up alone, down alone, and both directions at once (GB/s, total bytes moved).
     The e2e loop overlaps one step's downloads with the next step's uploads of other
     planes, so "both" uploads the planes while downloading the same number of bytes from
@@ -393,14 +391,12 @@ def host_link(torch, dev, host, p, planes, s_up, s_dn):
     host_scratch = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
 
     def up():
-        with torch.cuda.stream(s_up):
-            for k, c in planes:
-                p.field(k)[c].copy_(host[k][c], non_blocking=True)
+        for k, c in planes:
+            p.copy_plane(k, c, host[k][c], True, stream=s_up)
 
     def down():
-        with torch.cuda.stream(s_dn):
-            for k, c in planes:
-                host[k][c].copy_(p.field(k)[c], non_blocking=True)
+        for k, c in planes:
+            p.copy_plane(k, c, host[k][c], False, stream=s_dn)
 
     def down_scratch():
         with torch.cuda.stream(s_dn):

@@ -129,6 +129,15 @@ int soax_bind(soax_t h, int32_t field, int32_t comp, int32_t buf, void* dev_ptr)
 /* Which buffer set (0 or 1) currently holds the particles.  soax_sort_by_cell and
  * soax_permute flip it; soax_set_current sets it. */
 int soax_current(soax_t h, int32_t* buf);
+
+/* Copy plane (field, comp) of the live buffer set (its first n elements, n x the
+ * element size bytes) from host memory to the device (to_device = 1) or back
+ * (to_device = 0), as one cudaMemcpyAsync on stream.  host must stay valid until the
+ * copy has run; it is asynchronous for page-locked (pinned) host memory, otherwise the
+ * call returns when the copy is done.  SOAX_EINVAL for a bad field, component or
+ * direction, a NULL host pointer (n > 0) or an unbound plane; SOAX_ECUDA if the copy
+ * cannot be enqueued. */
+int soax_copy_plane(soax_t h, int32_t field, int32_t comp, void* host, int32_t to_device, void* stream);
 int soax_set_current(soax_t h, int32_t buf);
 
 /* Natural C layout of the AoS record of this schema (the structs of Listing 1 and 4):

@@ -176,6 +176,19 @@ class Particles:
                 a = torch.as_tensor(a)
                 dst[c][: a.shape[0]].copy_(a)
 
+    def copy_plane(self, name, comp, host, to_device, stream=None):
+        """soax_copy_plane: one live plane to (to_device=True) or from a host tensor or
+        array of the plane's element size and at least n elements, asynchronously on the
+        stream (host memory must be pinned for that, and must outlive the copy)."""
+        t = torch.as_tensor(host)
+        if t.device.type != "cpu" or not t.is_contiguous():
+            raise ValueError("copy_plane: host must be a contiguous CPU tensor or array")
+        plane = self.field(name)[comp]
+        if t.element_size() != plane.element_size() or t.numel() < self.n:
+            raise ValueError("copy_plane: host must hold n elements of the plane's size")
+        _check(lib().soax_copy_plane(self.h, self.fidx(name), int(comp), C.c_void_p(t.data_ptr()), int(bool(to_device)),
+                                     _stream(stream)), "soax_copy_plane")
+
     def numpy(self):
         """Live planes (the current size) as numpy arrays (synchronises)."""
         return {name: [t[:self.n].cpu().numpy() for t in self.field(name)] for name in self._names}

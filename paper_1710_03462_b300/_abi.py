@@ -38,6 +38,7 @@ SIGNATURES = {
     "soax_set_size": [_p, _i64],
     "soax_bind": [_p, _i32, _i32, _i32, _p],
     "soax_current": [_p, _P(_i32)],
+    "soax_copy_plane": [_p, _i32, _i32, _p, _i32, _p],
     "soax_set_current": [_p, _i32],
     "soax_aos_layout": [_p, _P(_i64), _P(_i64)],
     "soax_aos_to_soa": [_p, _p, _p],

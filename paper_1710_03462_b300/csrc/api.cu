@@ -164,6 +164,22 @@ extern "C" int soax_bind(soax_t h, int32_t field, int32_t comp, int32_t buf, voi
   return SOAX_OK;
 }
 
+extern "C" int soax_copy_plane(soax_t h, int32_t field, int32_t comp, void* host, int32_t to_device, void* stream) {
+  if (int e = check_handle(h)) return e;
+  if (field < 0 || field >= (int)h->fields.size()) return fail(SOAX_EINVAL, "soax_copy_plane: bad field");
+  if (comp < 0 || comp >= h->fields[field].ncomp) return fail(SOAX_EINVAL, "soax_copy_plane: bad component");
+  if (to_device != 0 && to_device != 1) return fail(SOAX_EINVAL, "soax_copy_plane: to_device must be 0 or 1");
+  if (h->n == 0) return SOAX_OK;
+  if (!host) return fail(SOAX_EINVAL, "soax_copy_plane: host is NULL");
+  const int p = h->fields[field].first_plane + comp;
+  void* dev = h->planes[h->current][p];
+  if (!dev) return fail(SOAX_EINVAL, "soax_copy_plane: plane not bound");
+  const size_t bytes = (size_t)h->n * (size_t)h->plane_esize[p];
+  const cudaError_t e = to_device ? cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, as_stream(stream))
+                                  : cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, as_stream(stream));
+  return e == cudaSuccess ? SOAX_OK : cuda_fail(e, "soax_copy_plane");
+}
+
 extern "C" int soax_current(soax_t h, int32_t* buf) {
   if (int e = check_handle(h)) return e;
   if (!buf) return fail(SOAX_EINVAL, "soax_current: NULL");

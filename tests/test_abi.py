@@ -96,6 +96,16 @@ def test_bind_validation_and_step_validation_without_gpu():
     assert L.soax_step_fused(h, C.byref(fl), -1, None) == -1
     assert b"nsteps" in L.soax_last_error()
     assert L.soax_step_fused(None, C.byref(fl), 1, None) == -1
+    # soax_copy_plane validates before any copy: field, component, direction, host
+    # pointer, and that the plane is bound.
+    buf = (C.c_double * 100)()
+    assert L.soax_copy_plane(h, 5, 0, buf, 1, None) == -1          # bad field
+    assert L.soax_copy_plane(h, 1, 3, buf, 1, None) == -1          # bad component
+    assert L.soax_copy_plane(h, 1, 0, buf, 2, None) == -1          # bad direction
+    assert L.soax_copy_plane(h, 1, 0, None, 0, None) == -1         # NULL host
+    assert L.soax_copy_plane(h, 1, 0, buf, 1, None) == -1          # plane not bound
+    assert b"not bound" in L.soax_last_error()
+    assert L.soax_copy_plane(None, 1, 0, buf, 1, None) == -1
     L.soax_destroy(h)
 
 
