@@ -361,14 +361,7 @@ def run_soax(args):
                 "copies": "soax_copy_plane per plane, uploads and downloads on two streams (step k's "
                           "download of a plane overlaps step k+1's uploads of the others)",
                 "link": link,
-                # Each step's state must come back before the next step's can go up, and the
-                # step needs all of it: per step at least the step's device time plus one
-                # round trip at the two directions' combined rate; the first upload and the
-                # last download of the run are not overlapped at all.
-                "floor": n * RK2_PER_STEP * e2e_steps / (
-                    e2e_steps * (max_el / args.steps + 2 * h2d / (link["both_GB/s"] * 1e9))
-                    + h2d / (link["h2d_GB/s"] * 1e9) + h2d / (link["d2h_GB/s"] * 1e9)
-                    - 2 * h2d / (link["both_GB/s"] * 1e9))},
+                "floor": e2e_floor(n * RK2_PER_STEP, e2e_steps, max_el / args.steps, h2d, link)},
         "gpu_launches": args.steps * (1 + sort_launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu_baseline(n) if world == 1 or rank == 0 else None,
@@ -378,6 +371,18 @@ def run_soax(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def e2e_floor(units_per_step, steps, step_seconds, state_bytes, link):
+    """The best e2e rate (units/s) the host link allows for `steps` bench steps that each
+    move state_bytes up and back: each step's state must come back before the next step's
+    can go up and the step needs all of it, so a step costs at least its device time plus
+    one round trip at the two directions' combined rate, and the run's first upload and
+    last download overlap nothing."""
+    both = 2 * state_bytes / (link["both_GB/s"] * 1e9)
+    total = (steps * step_seconds + (steps - 1) * both + state_bytes / (link["h2d_GB/s"] * 1e9)
+             + state_bytes / (link["d2h_GB/s"] * 1e9))
+    return units_per_step * steps / total
 
 
 def host_link(torch, dev, host, p, planes, s_up, s_dn):

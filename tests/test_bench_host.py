@@ -1,0 +1,56 @@
+"""bench.py's host-side arithmetic without a GPU: the committed ncu records are used only
+while they match the sources, the HBM roofline entry, and the e2e floor the host link
+sets."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_ncu_records_are_complete():
+    d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    assert {"k_step_soa_fused_gather", "k_step_soa", "k_adj_forward", "k_adj_reverse", "k_step_batched_fused",
+            "k_step_aos"} <= set(d)
+    for k, e in d.items():
+        assert len(e["source_hash"]) == 16, k
+        assert e["inst_per_particle_step"] > 0 and e["dram_bytes_per_launch_full_size"] > 0, k
+        assert os.path.exists(os.path.join(ROOT, e["summary"])), k
+
+
+def test_records_ignored_when_the_sources_differ(monkeypatch):
+    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    assert bench.ncu_record("k_step_soa_fused_gather") is None
+    assert bench.ncu_traffic("k_step_soa_fused_gather") is None
+    assert bench.hbm_roofline(72, 1000, 1e-6, "k_step_soa")["traffic"] is None
+
+
+def test_hbm_roofline(monkeypatch):
+    monkeypatch.setattr(bench, "measured_peaks", lambda: (6500.0, "measured"))
+    r = bench.hbm_roofline(72, 16777216, 0.5e-3)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6500.0
+    assert r["achieved"] == pytest.approx(72 * 16777216 / 0.5e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6500.0)
+
+
+def test_e2e_floor():
+    link = {"h2d_GB/s": 50.0, "d2h_GB/s": 50.0, "both_GB/s": 100.0}
+    # A full-duplex link (both directions at once at twice one direction's rate): the k
+    # steps' device time, k - 1 round trips between them at the combined rate (one
+    # direction's time each), and the first upload and the last download alone.
+    b, t, k, u = 1e9, 2e-3, 5, 1e9
+    per = b / 50e9
+    want = u * k / (k * t + (k - 1) * per + 2 * per)
+    assert bench.e2e_floor(u, k, t, b, link) == pytest.approx(want)
+    # One step: the upload, the step and the download in sequence.
+    assert bench.e2e_floor(u, 1, t, b, link) == pytest.approx(u / (t + 2 * per))
+    # A faster combined link can only raise the floor; the floor never beats the
+    # device time alone.
+    fast = dict(link, **{"both_GB/s": 200.0})
+    assert bench.e2e_floor(u, k, t, b, fast) > bench.e2e_floor(u, k, t, b, link)
+    assert bench.e2e_floor(u, k, t, b, link) < u / t
