@@ -133,6 +133,32 @@ def test_checkpointed_forward_equals_fused_step():
             assert u.tobytes() == v.tobytes()
 
 
+def test_checkpointed_forward_with_acceleration_equals_fused_step():
+    """With an acceleration field the checkpointed forward (its ACC kernel) stores the
+    same positions, velocities and last-stage accelerations as the fused step, and the
+    adjoint still runs (the acceleration is an output only, not differentiated)."""
+    n, K = 5003, 40
+    d = soax_inputs.wide_set(n, 6)
+    schema = [("pos", "f64", 3, "P"), ("vel", "f32", 3, "V"), ("acc", "f32", 3, "A")]
+    a = sx.Particles(schema, n, shadow=False)
+    b = sx.Particles(schema, n, shadow=False)
+    for q in (a, b):
+        q.load({"pos": d["pos"], "vel": d["vel"], "acc": d["acc"]})
+    f = sx.Flow(tau=0.15, dt=1e-3, acc="acc")
+    a.step_fused(f, K)
+    ws = b.adjoint_workspace(K, 16)
+    b.step_checkpointed(f, K, 16, ws)
+    x, y = a.numpy(), b.numpy()
+    for k in ("pos", "vel", "acc"):
+        for u, v in zip(x[k], y[k]):
+            assert u.tobytes() == v.tobytes(), k
+    assert not np.array_equal(y["acc"][0], d["acc"][0])
+    xt = [torch.from_numpy(p.copy()).cuda() for p in d["pos"]]
+    _, xb = b.minimage_loss(xt, ws)
+    _, _, g = b.step_adjoint(f, K, 16, ws, xb)
+    assert np.all(np.isfinite(g.cpu().numpy()))
+
+
 def test_zero_gradient_at_target():
     """Targets from the same forward: the loss and every gradient are exactly zero."""
     n, K = 2000, 64

@@ -135,6 +135,38 @@ def test_fused_wide_record_mass_tau_and_acc():
         assert np.array_equal(g[k][0], d[k][0])
 
 
+@pytest.mark.parametrize("form", ["acc_only", "tau_only"])
+def test_fused_wide_record_mixed_forms(form):
+    """The two mixed field forms of the wide record, each its own kernel: a stored
+    acceleration with a uniform tau (the check-free path applies) and tau from the mass
+    field without an acceleration, against the oracle."""
+    n, steps = 30001, 12
+    d = soax_inputs.wide_set(n, 5)
+    p = sx.Particles(sx.WIDE_SCHEMA, n)
+    p.load(d)
+    opos = [a.copy() for a in d["pos"]]
+    ovel = [a.copy() for a in d["vel"]]
+    if form == "acc_only":
+        p.step_fused(sx.Flow(tau=0.1, dt=5e-4, acc="acc"), steps)
+        oacc = [a.copy() for a in d["acc"]]
+        oracle.step_soa(opos, ovel, 1.0, 1.0, 1.0, 0.1, 5e-4, steps, acc=oacc)
+        taus = np.full(n, 0.1)
+    else:
+        p.step_fused(sx.Flow(dt=5e-4, tau_field="mass", tau_scale=0.1), steps)
+        oracle.step_soa(opos, ovel, 1.0, 1.0, 1.0, 0.0, 5e-4, steps, mass=d["mass"][0], tau_scale=0.1)
+        taus = 0.1 * d["mass"][0].astype(np.float64)
+    g = p.numpy()
+    assert_parity_fused(g["pos"], g["vel"], opos, ovel, d["pos"], d["vel"], taus, 1.0, 1.0, 1.0, 5e-4, steps)
+    if form == "acc_only":
+        for c in range(3):
+            assert np.allclose(g["acc"][c], oacc[c], rtol=1e-5, atol=1e-6)
+    else:
+        for c in range(3):
+            assert np.array_equal(g["acc"][c], d["acc"][c])  # not an output of this form
+    for k in ("id", "mass", "tag"):
+        assert np.array_equal(g[k][0], d[k][0])
+
+
 @pytest.mark.parametrize("A,B,C,tau,dt", [(1.5, 0.5, 1.3, 0.01, 1e-3), (0.7, 1.4, 0.9, 0.05, 1e-3),
                                           (1.2, 1.1, 0.6, 0.2, 5e-4)])
 def test_fused_amplitudes_and_stiff_tau(A, B, C, tau, dt):
@@ -222,16 +254,20 @@ def test_sort_by_keys_equals_sort_by_cell():
     assert np.all(np.diff(sk.astype(np.int64)) >= 0)
 
 
-@pytest.mark.parametrize("schema,grid", [("basic", 32), ("wide", 64), ("basic", 0)])
+@pytest.mark.parametrize("schema,grid", [("basic", 32), ("wide", 64), ("basic", 0), ("wide_acc_only", 64),
+                                         ("wide_tau_only", 0)])
 def test_permute_step_fused_equals_permute_then_step(schema, grid):
     """soax_permute_step_fused gives the bits of soax_permute followed by the fused step
-    (and its keys), for every field of the record, and flips the live set."""
+    (and its keys), for every field of the record and every field form of the step, and
+    flips the live set."""
     n = 50003
     if schema == "basic":
         d, sch, f = soax_inputs.basic_set(n, 31), sx.BASIC_SCHEMA, sx.Flow(tau=0.2, dt=1e-3)
     else:
         d, sch = soax_inputs.wide_set(n, 32), sx.WIDE_SCHEMA
-        f = sx.Flow(dt=5e-4, tau_field="mass", tau_scale=0.1, acc="acc")
+        f = {"wide": sx.Flow(dt=5e-4, tau_field="mass", tau_scale=0.1, acc="acc"),
+             "wide_acc_only": sx.Flow(tau=0.1, dt=5e-4, acc="acc"),
+             "wide_tau_only": sx.Flow(dt=5e-4, tau_field="mass", tau_scale=0.1)}[schema]
     rng = np.random.default_rng(5)
     perm = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
     a = sx.Particles(sch, n)
