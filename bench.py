@@ -74,11 +74,13 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="soax", choices=["soax", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
-    ap.add_argument("--only", choices=["euler", "adjoint", "batched", "aos"],
+    ap.add_argument("--only", choices=["euler", "adjoint", "batched", "aos", "fixed"],
                     help="run only this secondary row (profiling captures)")
     ap.add_argument("--n", type=int, default=None, help="particles (default: the row's workload)")
     ap.add_argument("--nens", type=int, default=None, help="--only batched: the first NENS ensembles")
     ap.add_argument("--fixed-tune", action="store_true", help="--only batched: a fixed launch shape, no autotuning")
+    ap.add_argument("--nsteps", type=int, nargs="*", default=None,
+                    help="--only fixed: steps per launch (default 10 and 20)")
     return ap.parse_args(argv)
 
 
@@ -636,6 +638,35 @@ def row_batched(sx, torch, dev, nens=None, fixed_tune=False):
     return out
 
 
+def row_fixed(sx, torch, dev, n, nsteps_list):
+    """Per-step and per-launch costs of the fused step: the bench's gather step (through
+    a near-identity permutation), the fused step with keys and the plain fused step, each
+    timed at every steps-per-launch in nsteps_list; with two or more, the slope and the
+    intercept of the first two (ms per step, ms per launch)."""
+    d = soax_inputs.basic_set(n, WL["seed"])
+    p = sx.Particles(sx.BASIC_SCHEMA, n, device=dev)
+    p.load(d)
+    ws = p.sort_workspace(WL["grid"])
+    f = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
+    keys = p.step_fused(f, RK2_PER_STEP, grid=WL["grid"])
+    perm = p.sort_perm(WL["grid"], keys, ws)[1]
+    keys = p.step_fused(f, RK2_PER_STEP, grid=WL["grid"], keys=keys, perm=perm)
+    perm = p.sort_perm(WL["grid"], keys, ws)[1]  # near-identity from here on
+    forms = (("gather+keys", lambda ns: p.step_fused(f, ns, grid=WL["grid"], keys=keys, perm=perm)),
+             ("fused+keys", lambda ns: p.step_fused(f, ns, grid=WL["grid"], keys=keys)),
+             ("fused", lambda ns: p.step_fused(f, ns)))
+    out = {}
+    for name, fn in forms:
+        ms = {ns: _time(torch, lambda: fn(ns), reps=5) * 1e3 for ns in nsteps_list}
+        row = {"ms_per_launch": ms}
+        if len(nsteps_list) >= 2:
+            a, b = nsteps_list[0], nsteps_list[1]
+            per = (ms[b] - ms[a]) / (b - a)
+            row.update(ms_per_step=per, ms_fixed=ms[a] - a * per)
+        out[name] = row
+    return out
+
+
 def secondary_rows(sx, torch, p, d, dev):
     n = p.n
     flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
@@ -657,6 +688,8 @@ def run_only(args):
         row = row_adjoint(sx, torch, dev, args.n)
     elif args.only == "batched":
         row = row_batched(sx, torch, dev, args.nens, args.fixed_tune)
+    elif args.only == "fixed":
+        row = row_fixed(sx, torch, dev, args.n or WL["n"], args.nsteps or [RK2_PER_STEP, 2 * RK2_PER_STEP])
     else:
         n = args.n or WL["n"]
         flow = sx.Flow(A=WL["A"], B=WL["B"], C=WL["C"], tau=WL["tau"], dt=WL["dt"])
