@@ -151,7 +151,12 @@ __device__ __forceinline__ void step_aos_loop(const AosArgs& a, const StepC& kc,
     float v[3] = {vp[0], vp[1], vp[2]}, acc[3];
     StepC k = kc;
     if (a.tau_off >= 0) set_inv_tau(k, ff_inv_tau(a.e.tsf, *reinterpret_cast<const float*>(r + a.tau_off)));
-    rk2_step<ACC>(k, tg, p, v, acc);
+    // The SoA step's dispatch (step_group with one particle): straight-line code within
+    // the shift series, the per-coordinate checks otherwise; the same bits either way.
+    if (near_shift(k, v))
+      rk2_step_fast<ACC, true>(k, tg, p, v, acc);
+    else
+      rk2_step_fast<ACC, false>(k, tg, p, v, acc);
     double* pw = reinterpret_cast<double*>(r + a.pos_off);
     float* vw = reinterpret_cast<float*>(r + a.vel_off);
     pw[0] = p[0]; pw[1] = p[1]; pw[2] = p[2];
