@@ -59,7 +59,7 @@ def _diverged(p, d, th, K, dt=1e-3, max_frac=1e-3):
     return bad
 
 
-@pytest.mark.parametrize("n,K,C", [(1, 5, 32), (1000, 70, 32), (4099, 100, 32), (513, 64, 8)])
+@pytest.mark.parametrize("n,K,C", [(1, 5, 32), (1000, 70, 32), (4099, 100, 32), (513, 64, 8), (700, 10, 1)])
 def test_adjoint_vs_oracle(n, K, C):
     d = soax_inputs.basic_set(n, n)
     xt = _target(d, K)
@@ -157,6 +157,30 @@ def test_checkpointed_forward_with_acceleration_equals_fused_step():
     _, xb = b.minimage_loss(xt, ws)
     _, _, g = b.step_adjoint(f, K, 16, ws, xb)
     assert np.all(np.isfinite(g.cpu().numpy()))
+
+
+def test_zero_steps_passes_the_seed_through():
+    """K = 0: no step, so x̄0 = x̄K and v̄0 = v̄K (to the float-pair precision the reverse
+    carries adjoints in: 48 significant bits, so binary64 seeds come back within 2^-47
+    relative, and exactly where they fit in 48 bits) and the parameter gradients are zero."""
+    n = 3000
+    d = soax_inputs.basic_set(n, 8)
+    p = sx.Particles(SCHEMA, n, shadow=False)
+    p.load({"pos": d["pos"], "vel": d["vel"]})
+    f = sx.Flow()
+    ws = p.adjoint_workspace(0, 32)
+    p.step_checkpointed(f, 0, 32, ws)
+    xt = [torch.from_numpy(np.roll(a, 1).copy()).cuda() for a in d["pos"]]
+    _, xb = p.minimage_loss(xt, ws)
+    vk = [torch.full((n,), 0.25, dtype=torch.float64, device="cuda") for _ in range(3)]
+    xb0, vb0, g = p.step_adjoint(f, 0, 32, ws, xb, vk)
+    for c in range(3):
+        assert torch.allclose(xb0[c], xb[c], rtol=2.0 ** -47, atol=0.0)
+        assert torch.equal(vb0[c], vk[c])  # 0.25 fits in 48 bits
+    assert np.all(g.cpu().numpy() == 0.0)
+    g2 = p.numpy()
+    for c in range(3):
+        assert np.array_equal(g2["pos"][c], d["pos"][c]) and np.array_equal(g2["vel"][c], d["vel"][c])
 
 
 def test_zero_gradient_at_target():
