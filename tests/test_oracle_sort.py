@@ -1,5 +1,6 @@
 """Pins of the oracle's cell keys, stable argsort and permute: exact rational floor
-division, brute-force O(N^2) stable selection, numpy's stable sort, and the sort
+division away from cell boundaries and correctly rounded rational arithmetic at them,
+brute-force O(N^2) stable selection, numpy's stable sort, and the sort
 invariants (keys nondecreasing, perm a bijection, equal keys keep their order, every
 field permuted alike)."""
 from fractions import Fraction
@@ -54,6 +55,33 @@ def test_keys_boundaries():
     z = np.array([0.0, 0.0, 0.0, below])
     k = oracle.cell_keys(x, y, z, G)
     assert k.tolist() == [0, G - 1, (G - 1) * G, (G - 1) * G * G]
+
+
+def test_keys_at_cell_boundaries_exact_rounding():
+    """Within a few ulps of cell boundaries the key is floor(RN(x RN(G / 2pi))): two
+    binary64 roundings, taken here with exact rational arithmetic (Python's Fraction
+    converts to the correctly rounded double), independently of the oracle's code.  A
+    key that skipped either rounding (x c in extended precision, or c = G / 2pi kept
+    exact) differs from this at some of these points."""
+    for G in (32, 64, 7):
+        c = float(Fraction(G) / Fraction(TWO_PI))           # RN(G / 2pi)
+        xs = []
+        for k in range(1, G):
+            x0 = float(Fraction(k) / Fraction(c))            # nearest double to the boundary k / c
+            x = x0
+            for _ in range(4):
+                x = np.nextafter(x, 0.0)
+            for _ in range(9):                               # x0 - 4 ulp .. x0 + 4 ulp
+                xs.append(x)
+                x = np.nextafter(x, 8.0)
+        xs = np.array(xs)
+        exp = [min(int(float(Fraction(float(x)) * Fraction(c))), G - 1) for x in xs]  # floor(RN(x c))
+        zeros = np.zeros_like(xs)
+        assert oracle.cell_keys(xs, zeros, zeros, G).tolist() == exp
+        assert oracle.cell_keys(zeros, xs, zeros, G).tolist() == [e * G for e in exp]
+        assert oracle.cell_keys(zeros, zeros, xs, G).tolist() == [e * G * G for e in exp]
+        # Both sides of every boundary occur, so the points do test the rounding.
+        assert len(set(exp)) == G
 
 
 def _selection_stable(keys):
