@@ -528,7 +528,7 @@ def row_aos(sx, torch, p, flow):
     aos = p.to_aos()
     t_rt = _time(torch, lambda: (p.to_aos(aos), p.from_aos(aos)), reps=5)
     rt = {"ms": t_rt * 1e3, "GB/s": 176 * n / t_rt / 1e9, "bytes_per_particle": 176,
-          "roofline": hbm_roofline(176, n, t_rt)}
+          "roofline": hbm_roofline(176, n, t_rt, "aos_soa_roundtrip")}
     t_aos = _time(torch, lambda: p.step_aos(aos, flow, 1), reps=3)
     t_soa = _time(torch, lambda: p.step(flow, 1), reps=3)
     st = {"particle-steps/s": n / t_aos, "algorithmic_GB/s": 72 * n / t_aos / 1e9,
