@@ -451,6 +451,7 @@ def euler_replica(sx, torch, n, dev):
     t_comp = _time(torch, lambda: q.euler(1e-3, per_component=True), reps=10)
     out["soa_fused_ns_per_particle"] = t_fused / n * 1e9
     out["soa_fused_GB/s"] = 36 * n / t_fused / 1e9
+    out["roofline"] = hbm_roofline(36, n, t_fused)
     out["soa_per_component_ns_per_particle"] = t_comp / n * 1e9
     del q
     for size in (0, 32):
