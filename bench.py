@@ -77,6 +77,7 @@ def parse_args(argv=None):
     ap.add_argument("--only", choices=["euler", "adjoint", "batched", "aos", "fixed"],
                     help="run only this secondary row (profiling captures)")
     ap.add_argument("--n", type=int, default=None, help="particles (default: the row's workload)")
+    ap.add_argument("--e2e-chunks", type=int, default=16, help="pieces per soax_step_host call in the e2e loop")
     ap.add_argument("--nens", type=int, default=None, help="--only batched: the first NENS ensembles")
     ap.add_argument("--fixed-tune", action="store_true", help="--only batched: a fixed launch shape, no autotuning")
     ap.add_argument("--nsteps", type=int, nargs="*", default=None,
@@ -111,22 +112,43 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
-def source_hash():
+CSRC = os.path.join(ROOT, "paper_1710_03462_b300", "csrc")
+
+
+def unit_sources(unit):
+    """The files a kernel's code comes from: its translation unit under csrc/, every
+    local header it includes (transitively), and the build script (compiler flags)."""
+    seen, todo = [], [os.path.join(CSRC, unit)]
+    while todo:
+        f = os.path.normpath(todo.pop())
+        if f in seen:
+            continue
+        seen.append(f)
+        with open(f) as fh:
+            for line in fh:
+                line = line.strip()
+                if line.startswith("#include \""):
+                    todo.append(os.path.join(os.path.dirname(f), line.split('"')[1]))
+    return sorted(seen) + [os.path.join(ROOT, "paper_1710_03462_b300", "build.py")]
+
+
+def source_hash(unit):
     h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1710_03462_b300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in unit_sources(unit):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_record(kernel):
     """The committed ncu figures of kernel (profiles/ncu_traffic.json) if they were taken
-    on the current sources; else None."""
+    on the current sources of its translation unit; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             j = json.load(fh)
         e = j.get(kernel)
-        if e and e.get("source_hash") == source_hash():
+        if e and e.get("source_hash") == source_hash(e["unit"]):
             return e
     except (OSError, ValueError, KeyError, TypeError):
         pass
@@ -308,32 +330,26 @@ def run_soax(args):
     units = n * RK2_PER_STEP * args.steps
     tot_units, max_el = aggregate(units, elapsed, dev)
 
-    # e2e through the C ABI with host buffers: the state goes up and comes back every
-    # bench step (pinned memory, one soax_copy_plane per plane).  Uploads run on one copy
-    # stream, downloads on another, so the link's two directions work at once: plane q's
-    # upload for step k + 1 waits only for plane q's download of step k (the same host
-    # buffer and device plane), and the step waits for all of its uploads.
+    # e2e through the C ABI with host buffers: the state lives in pinned host memory and
+    # every bench step is one soax_step_host call, which uploads it, steps it, sorts it
+    # and downloads it in pieces (uploads overlap the steps of the pieces already up;
+    # downloads overlap the next call's uploads).  Calls are queued back to back: the
+    # library orders each piece's upload after the previous call's download of it.
     host = {k: [torch.from_numpy(a).pin_memory() for a in v] for k, v in d.items()}
     e2e_steps = max(1, min(args.steps, 20))  # the run's first upload and last download amortised over 20 steps
     h2d = sum(t.numel() * t.element_size() for v in host.values() for t in v)
     planes = [(k, c) for k, v in host.items() for c in range(len(v))]
     s_up, s_dn = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    down = {}
+    e2e_ws = p.sort_workspace(WL["grid"])
+    p.step_host(host, flow, 0, WL["grid"], nchunks=args.e2e_chunks, ws=e2e_ws, stream=stream, up_stream=s_up,
+                down_stream=s_dn)  # creates the call's events outside the timed region
     torch.cuda.synchronize(dev)
+    for k, c in planes:  # the host home holds the set the device run started from
+        host[k][c].copy_(torch.from_numpy(d[k][c]))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for k, c in planes:
-            if (k, c) in down:
-                s_up.wait_event(down[(k, c)])
-            p.copy_plane(k, c, host[k][c], True, stream=s_up)  # soax_copy_plane, host -> device
-        stream.wait_stream(s_up)
-        bench_step()
-        s_dn.wait_stream(stream)
-        for k, c in planes:
-            p.copy_plane(k, c, host[k][c], False, stream=s_dn)  # device -> host
-            ev = torch.cuda.Event()
-            ev.record(s_dn)
-            down[(k, c)] = ev
+        p.step_host(host, flow, RK2_PER_STEP, WL["grid"], nchunks=args.e2e_chunks, ws=e2e_ws, stream=stream,
+                    up_stream=s_up, down_stream=s_dn)
     torch.cuda.synchronize(dev)
     e2e_el = time.perf_counter() - t0
     e2e_units, e2e_max = aggregate(n * RK2_PER_STEP * e2e_steps, e2e_el, dev)
@@ -363,10 +379,10 @@ def run_soax(args):
         "sort_ms": statistics.mean(sort_ms),
         "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d, "steps": e2e_steps,
-                "copies": "soax_copy_plane per plane, uploads and downloads on two streams (step k's "
-                          "download of a plane overlaps step k+1's uploads of the others)",
+                "copies": f"soax_step_host, {args.e2e_chunks} pieces per call: piece uploads overlap the "
+                          "steps of the pieces already up, downloads overlap the next call's uploads",
                 "link": link,
-                "floor": e2e_floor(n * RK2_PER_STEP, e2e_steps, max_el / args.steps, h2d, link)},
+                "floor": e2e_floor(n * RK2_PER_STEP, e2e_steps, statistics.mean(sort_ms) / 1e3, h2d, link)},
         "gpu_launches": args.steps * (1 + sort_launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu_baseline(n) if world == 1 or rank == 0 else None,
@@ -378,14 +394,15 @@ def run_soax(args):
     return 0
 
 
-def e2e_floor(units_per_step, steps, step_seconds, state_bytes, link):
-    """The best e2e rate (units/s) the host link allows for `steps` bench steps that each
-    move state_bytes up and back: each step's state must come back before the next step's
-    can go up and the step needs all of it, so a step costs at least its device time plus
-    one round trip at the two directions' combined rate, and the run's first upload and
-    last download overlap nothing."""
+def e2e_floor(units_per_step, steps, gap_seconds, state_bytes, link):
+    """The best e2e rate (units/s) the host link allows for `steps` sort intervals that
+    each move state_bytes up and back: the first upload and the last download overlap
+    nothing, the k - 1 round trips between them move at most at the two directions'
+    combined rate, and in every interval the link waits gap_seconds of device work that
+    needs all of the upload and precedes all of the download (the sort: every key before
+    it, every sorted particle after it)."""
     both = 2 * state_bytes / (link["both_GB/s"] * 1e9)
-    total = (steps * step_seconds + (steps - 1) * both + state_bytes / (link["h2d_GB/s"] * 1e9)
+    total = (steps * gap_seconds + (steps - 1) * both + state_bytes / (link["h2d_GB/s"] * 1e9)
              + state_bytes / (link["d2h_GB/s"] * 1e9))
     return units_per_step * steps / total
 
@@ -393,9 +410,9 @@ def e2e_floor(units_per_step, steps, step_seconds, state_bytes, link):
 def host_link(torch, dev, host, p, planes, s_up, s_dn):
     """The host link's rates for the e2e state (pinned memory, one soax_copy_plane per plane): all
     planes up alone, down alone, and both directions at once (GB/s, total bytes moved).
-    The e2e loop overlaps one step's downloads with the next step's uploads of other
-    planes, so "both" uploads the planes while downloading the same number of bytes from
-    a separate device buffer into a separate pinned buffer."""
+    The e2e loop overlaps one call's downloads with the next call's uploads, so "both"
+    uploads the planes while downloading the same number of bytes from a separate device
+    buffer into a separate pinned buffer."""
     nbytes = sum(t.numel() * t.element_size() for v in host.values() for t in v)
     dev_scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     host_scratch = torch.empty(nbytes, dtype=torch.uint8).pin_memory()

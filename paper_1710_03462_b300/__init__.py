@@ -189,6 +189,50 @@ class Particles:
         _check(lib().soax_copy_plane(self.h, self.fidx(name), int(comp), C.c_void_p(t.data_ptr()), int(bool(to_device)),
                                      _stream(stream)), "soax_copy_plane")
 
+    def host_planes(self, pinned=True):
+        """Host tensors shaped like the planes ({name: [comp0, ...]}, n elements each),
+        page-locked by default: the host home of a set that step_host streams."""
+        out = {}
+        for name, dt, nc, _ in self.schema:
+            ts = [torch.empty(self.n, dtype=TORCH_DTYPES[dt]) for _ in range(nc)]
+            out[name] = [t.pin_memory() for t in ts] if pinned else ts
+        return out
+
+    def step_host(self, host, f: Flow, nsteps, grid, nchunks=0, ws=None, stream=None, up_stream=None,
+                  down_stream=None):
+        """soax_step_host: one sort interval of the set held in the host tensors `host`
+        ({name: [comp0, ...]}, contiguous CPU tensors of the planes' element sizes and n
+        elements, pinned for overlap): uploaded in nchunks pieces (0: the library's
+        default), stepped nsteps fused steps with cell keys on the grid^3 grid, sorted by
+        cell, gathered and downloaded back into `host`, all asynchronously: the host
+        tensors are final once down_stream has passed the call (synchronise it or the
+        device), the device planes once `stream` has.  Copies run on up_stream and
+        down_stream (two streams of this object when not given).  Returns the permutation
+        (int32 view into ws)."""
+        ptrs = []
+        for name, dt, nc, _ in self.schema:
+            comps = host[name]
+            if len(comps) != nc:
+                raise ValueError(f"step_host: field {name} needs {nc} host tensors")
+            for t in comps:
+                if t.device.type != "cpu" or not t.is_contiguous():
+                    raise ValueError("step_host: host tensors must be contiguous CPU tensors")
+                if t.element_size() != torch.empty(0, dtype=TORCH_DTYPES[dt]).element_size() or t.numel() < self.n:
+                    raise ValueError(f"step_host: field {name} needs n elements of its size")
+                ptrs.append(t.data_ptr())
+        ws = self.sort_workspace(grid) if ws is None else ws
+        if up_stream is None or down_stream is None:
+            if getattr(self, "_copy_streams", None) is None:
+                self._copy_streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
+            up_stream = up_stream or self._copy_streams[0]
+            down_stream = down_stream or self._copy_streams[1]
+        arr = (C.c_void_p * max(len(ptrs), 1))(*ptrs)
+        fl = self.flow(f)
+        _check(lib().soax_step_host(self.h, arr, C.byref(fl), int(nsteps), int(grid), int(nchunks), _ptr(ws),
+                                    ws.numel(), _stream(stream), _stream(up_stream), _stream(down_stream)),
+               "soax_step_host")
+        return self.sort_results(grid, ws)[1]
+
     def numpy(self):
         """Live planes (the current size) as numpy arrays (synchronises)."""
         return {name: [t[:self.n].cpu().numpy() for t in self.field(name)] for name in self._names}

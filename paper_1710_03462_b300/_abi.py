@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/soax.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/soax.h and include/soax_host.h (argument
+marshalling only)."""
 import ctypes as C
 import os
 
@@ -28,7 +29,7 @@ class soax_tune(C.Structure):
 _p, _i32, _i64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
 _P = C.POINTER
 
-# Every function include/soax.h declares, with its argument types.
+# Every function include/soax.h and include/soax_host.h declare, with its argument types.
 SIGNATURES = {
     "soax_version": [],
     "soax_last_error": [],
@@ -75,6 +76,7 @@ SIGNATURES = {
     "soax_step_batched": [_P(_p), _P(soax_flow), _i32, _i32, _P(soax_tune), _p, _sz, _p],
     "soax_autotune": [_P(_p), _P(soax_flow), _i32, _i32, _p, _sz, _P(soax_tune), _p],
     "soax_sync": [_p],
+    "soax_step_host": [_p, _P(_p), _P(soax_flow), _i32, _i32, _i32, _p, _sz, _p, _p, _p],
 }
 EXPORTS = list(SIGNATURES)
 

@@ -132,7 +132,12 @@ extern "C" int soax_create(const soax_field_desc* fields, int32_t nfields, int64
   return SOAX_OK;
 }
 
+namespace soax {
+void release_host_pipe(const soax_s* h);  // host_step.cu: the events of soax_step_host
+}
+
 extern "C" int soax_destroy(soax_t h) {
+  if (h) soax::release_host_pipe(h);
   delete h;
   return SOAX_OK;
 }

@@ -272,9 +272,10 @@ struct PermArgs {
   void* out[kMaxPlanes];
   int32_t es[kMaxPlanes];
   int nplanes;
-  int64_t n;
+  int64_t n;     // outputs: out_f[i] for 0 <= i < n
+  int64_t nsrc;  // inputs: perm entries must be < nsrc
   const uint32_t* perm;
-  int* status;  // device status word: an index >= n is recorded here and not read
+  int* status;  // device status word: an index >= nsrc is recorded here and not read
 };
 
 __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArgs a) {
@@ -282,13 +283,13 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArg
   if (i0 >= a.n) return;
   if (i0 + 4 <= a.n) {
     uint4 p = *reinterpret_cast<const uint4*>(a.perm + i0);
-    if (p.x >= a.n || p.y >= a.n || p.z >= a.n || p.w >= a.n) {
-      // Not a permutation of 0..n-1: report and gather element 0 instead.
+    if (p.x >= a.nsrc || p.y >= a.nsrc || p.z >= a.nsrc || p.w >= a.nsrc) {
+      // Not a permutation of 0..nsrc-1: report and gather element 0 instead.
       atomicExch(a.status, (int)SOAX_EINVAL);
-      if (p.x >= a.n) p.x = 0;
-      if (p.y >= a.n) p.y = 0;
-      if (p.z >= a.n) p.z = 0;
-      if (p.w >= a.n) p.w = 0;
+      if (p.x >= a.nsrc) p.x = 0;
+      if (p.y >= a.nsrc) p.y = 0;
+      if (p.z >= a.nsrc) p.z = 0;
+      if (p.w >= a.nsrc) p.w = 0;
     }
     for (int f = 0; f < a.nplanes; ++f) {
       const int es = a.es[f];
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArg
   } else {
     for (int64_t i = i0; i < a.n; ++i) {
       uint32_t p = a.perm[i];
-      if (p >= a.n) {
+      if (p >= a.nsrc) {
         atomicExch(a.status, (int)SOAX_EINVAL);
         p = 0;
       }
@@ -444,6 +445,43 @@ extern "C" int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* va
   return SOAX_OK;
 }
 
+namespace soax {
+
+// Particles [i0, i0 + cnt) of the other buffer set from the live set through perm
+// (out_f[i] = in_f[perm[i]], perm indexed like the particles); the live set does not
+// flip.  i0 a multiple of 4 (aligned vector access of perm and of the outputs); both
+// buffer sets bound and perm 16-byte aligned (the caller checks).
+int permute_range(soax_t h, const uint32_t* perm, int64_t i0, int64_t cnt, void* stream) {
+  const int src = h->current, dst = src ^ 1;
+  if (cnt <= 0) return SOAX_OK;
+  if (i0 % 4 != 0) return fail(SOAX_EINVAL, "permute_range: first index not a multiple of 4");
+  PermArgs a;
+  for (int p = 0; p < h->nplanes; ++p) {
+    a.in[p] = h->planes[src][p];
+    a.out[p] = static_cast<char*>(h->planes[dst][p]) + i0 * h->plane_esize[p];
+    a.es[p] = h->plane_esize[p];
+  }
+  a.nplanes = h->nplanes;
+  a.n = cnt;
+  a.nsrc = h->n;
+  a.perm = perm + i0;
+  a.status = status_word();
+  if (!a.status) return fail(SOAX_ECUDA, "soax_permute: status word");
+  k_permute<<<grid_for((cnt + 3) / 4, 256), 256, 0, as_stream(stream)>>>(a);
+  return check_launch("soax_permute");
+}
+
+// Byte offsets of the cell-key region and of the permutation in a workspace of
+// soax_sort_workspace_bytes bytes (the key region takes a caller's keys, as in
+// soax_sort_by_cell).
+void sort_ws_regions(int64_t n, int grid, size_t* off_keys, size_t* off_perm) {
+  const SortWs w = sort_ws_plan(n, grid);
+  *off_keys = w.off_keys;
+  *off_perm = w.off_perm;
+}
+
+}  // namespace soax
+
 extern "C" int soax_permute(soax_t h, const uint32_t* perm, void* stream) {
   if (int r = check_handle(h)) return r;
   const int src = h->current, dst = src ^ 1;
@@ -455,19 +493,7 @@ extern "C" int soax_permute(soax_t h, const uint32_t* perm, void* stream) {
   if (!aligned16(perm)) return fail(SOAX_EALIGN, "soax_permute: perm not 16-byte aligned");
   if (int r = live_planes_bound(h, src)) return r;
   if (int r = live_planes_bound(h, dst)) return r;
-  PermArgs a;
-  for (int p = 0; p < h->nplanes; ++p) {
-    a.in[p] = h->planes[src][p];
-    a.out[p] = h->planes[dst][p];
-    a.es[p] = h->plane_esize[p];
-  }
-  a.nplanes = h->nplanes;
-  a.n = h->n;
-  a.perm = perm;
-  a.status = status_word();
-  if (!a.status) return fail(SOAX_ECUDA, "soax_permute: status word");
-  k_permute<<<grid_for((h->n + 3) / 4, 256), 256, 0, as_stream(stream)>>>(a);
-  if (int r = check_launch("soax_permute")) return r;
+  if (int r = soax::permute_range(h, perm, 0, h->n, stream)) return r;
   h->current = dst;
   return SOAX_OK;
 }

@@ -1,6 +1,7 @@
 """The C ABI without a GPU: the library builds and loads, exports every symbol that
-include/soax.h declares, and validates arguments on the host (no device work)."""
+include/*.h declare, and validates arguments on the host (no device work)."""
 import ctypes as C
+import glob
 import os
 import re
 
@@ -14,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "soax.h")).read()
+    src = "".join(open(f).read() for f in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     return sorted(set(re.findall(r"^(?:int|const char\*)\s+(soax_\w+)\s*\(", src, re.M)))
 
 
@@ -130,6 +131,48 @@ def test_empty_handle_is_a_no_op():
     assert L.soax_current(h, C.byref(cur)) == 0 and cur.value == 1
     assert L.soax_step_fused(h, C.byref(fl), 3, None) == 0
     assert L.soax_soa_to_aos(h, None, None) == 0
+    L.soax_destroy(h)
+
+
+def test_step_host_validation_without_gpu():
+    # soax_step_host checks everything on the host before any event, copy or launch.
+    L = sx.lib()
+    fl = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 1, 2, -1)
+    bad = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 2, 1, -1)  # pos/vel swapped
+    rc, h0 = _create(sx.BASIC_SCHEMA, 100)
+    assert L.soax_step_host(h0, (C.c_void_p * 7)(*([0x1000] * 7)), C.byref(fl), 10, 32, 0, C.c_void_p(0x10000),
+                            1 << 30, None, None, None) == -8    # planes not bound
+    L.soax_destroy(h0)
+    rc, h = _create(sx.BASIC_SCHEMA, 100)
+    for f, nc in enumerate((1, 3, 3)):                            # fake device addresses, never touched
+        for c in range(nc):
+            for b in (0, 1):
+                assert L.soax_bind(h, f, c, b, C.c_void_p(0x100000 * (1 + 8 * f + 2 * c + b))) == 0
+    host = (C.c_void_p * 7)(*([0x1000] * 7))
+    ws = C.c_void_p(0x10000)
+    args = lambda **k: dict(dict(host=host, fl=C.byref(fl), nsteps=10, grid=32, nchunks=0, ws=ws, wsb=1 << 30), **k)
+
+    def call(**k):
+        a = args(**k)
+        return L.soax_step_host(h, a["host"], a["fl"], a["nsteps"], a["grid"], a["nchunks"], a["ws"], a["wsb"],
+                                None, None, None)
+    assert call(nsteps=-1) == -1
+    assert call(grid=0) == -1 and call(grid=1025) == -1
+    assert call(nchunks=-1) == -1 and call(nchunks=1025) == -1
+    assert b"nchunks" in L.soax_last_error()
+    assert call(fl=C.byref(bad)) == -2
+    assert call(host=None) == -1
+    holes = (C.c_void_p * 7)(*([0x1000] * 6 + [0]))
+    assert call(host=holes) == -1 and b"host plane 6" in L.soax_last_error()
+    assert call(wsb=16) == -6
+    assert call(ws=C.c_void_p(0x10008)) == -3
+    assert L.soax_step_host(None, host, C.byref(fl), 1, 32, 0, ws, 1 << 30, None, None, None) == -1
+    L.soax_destroy(h)
+    # An empty set moves nothing: the live set flips, as after soax_permute.
+    rc, h = _create(sx.BASIC_SCHEMA, 0)
+    cur = C.c_int32()
+    assert L.soax_step_host(h, None, C.byref(fl), 10, 32, 0, None, 0, None, None, None) == 0
+    assert L.soax_current(h, C.byref(cur)) == 0 and cur.value == 1
     L.soax_destroy(h)
 
 
