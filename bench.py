@@ -439,6 +439,19 @@ def host_link(torch, dev, host, p, planes, s_up, s_dn):
             fn()
         torch.cuda.synchronize(dev)
         out[name] = moved * 3 / (time.perf_counter() - t0) / 1e9
+    # Each direction's own rate while both run, started together (CUDA events on the two
+    # copy streams): the e2e pipeline waits on the slower one, piece by piece.
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize(dev)
+    ev[0].record(s_up)
+    s_dn.wait_event(ev[0])
+    up()
+    down_scratch()
+    ev[1].record(s_up)
+    ev[2].record(s_dn)
+    torch.cuda.synchronize(dev)
+    out["both_h2d_GB/s"] = nbytes / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e9
+    out["both_d2h_GB/s"] = nbytes / (ev[0].elapsed_time(ev[2]) / 1e3) / 1e9
     return out
 
 

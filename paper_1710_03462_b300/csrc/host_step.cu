@@ -82,6 +82,29 @@ int ensure_events(Pipe& p, int nchunks) {
   return SOAX_OK;
 }
 
+// Piece boundaries 0 = cut[0] < cut[1] < ... < cut[C] = n, every inner one a multiple of
+// kChunkAlign.  The first piece's download and the last piece's upload each run with the
+// other link direction idle, and the last piece's step sits before the sort: with four or
+// more pieces those two are a quarter of the others.
+std::vector<int64_t> plan_pieces(int64_t n, int64_t want) {
+  const int64_t units = (n + kChunkAlign - 1) / kChunkAlign;
+  if (want > units) want = units;
+  std::vector<int64_t> w(want, 4);
+  if (want >= 4) w.front() = w.back() = 1;
+  int64_t total = 0;
+  for (int64_t x : w) total += x;
+  std::vector<int64_t> cut{0};
+  int64_t acc = 0;
+  for (int64_t i = 0; i < want; ++i) {
+    acc += w[i];
+    int64_t c = (units * acc + total / 2) / total * kChunkAlign;
+    if (c > n) c = n;
+    if (c > cut.back()) cut.push_back(c);
+  }
+  if (cut.back() != n) cut.push_back(n);
+  return cut;
+}
+
 // The handle restricted to particles [i0, i0 + cnt) in both buffer sets: the same
 // schema, plane pointers advanced by i0 elements.
 soax_s view(const soax_s& h, int64_t i0, int64_t cnt) {
@@ -141,12 +164,8 @@ int step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, 
   if (int r = live_planes_bound(h, h->current)) return r;
   if (int r = live_planes_bound(h, h->current ^ 1)) return r;
 
-  // Pieces of L particles (a multiple of kChunkAlign), the last one ragged.
-  const int64_t want = nchunks ? nchunks : kDefaultChunks;
-  const int64_t units = (n + kChunkAlign - 1) / kChunkAlign;
-  const int64_t per = (units + want - 1) / want;  // alignment units per piece
-  const int64_t L = per * kChunkAlign;
-  const int C = (int)((n + L - 1) / L);
+  const std::vector<int64_t> cut = plan_pieces(n, nchunks ? nchunks : kDefaultChunks);
+  const int C = (int)cut.size() - 1;
 
   std::lock_guard<std::mutex> lk(g_mu);
   Pipe& P = g_pipes[h];
@@ -172,7 +191,7 @@ int step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, 
 
   // 1. Upload and step piece by piece.
   for (int c = 0; c < C; ++c) {
-    const int64_t a = (int64_t)c * L, cnt = (a + L <= n ? L : n - a);
+    const int64_t a = cut[c], cnt = cut[c + 1] - cut[c];
     if (P.pending)
       for (size_t j = 0; j < P.lo.size(); ++j)
         if (P.lo[j] < a + cnt && a < P.hi[j])
@@ -194,7 +213,7 @@ int step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, 
 
   // 3. Gather and download piece by piece.
   for (int c = 0; c < C; ++c) {
-    const int64_t a = (int64_t)c * L, cnt = (a + L <= n ? L : n - a);
+    const int64_t a = cut[c], cnt = cut[c + 1] - cut[c];
     if (int r = permute_range(h, perm, a, cnt, stream)) return failed(r);
     if (int r = record(P.gathered[c], stream)) return failed(r);
     if (int r = wait(down, P.gathered[c])) return failed(r);
@@ -210,12 +229,8 @@ int step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, 
   // not hold its uploads behind this call's downloads (they overlap them, piece by
   // piece).  The host planes are final once down_stream has passed the call.
 
-  P.lo.assign(C, 0);
-  P.hi.assign(C, 0);
-  for (int c = 0; c < C; ++c) {
-    P.lo[c] = (int64_t)c * L;
-    P.hi[c] = P.lo[c] + L < n ? P.lo[c] + L : n;
-  }
+  P.lo.assign(cut.begin(), cut.end() - 1);
+  P.hi.assign(cut.begin() + 1, cut.end());
   P.pending = true;
   h->current = other;
   return SOAX_OK;
