@@ -52,7 +52,9 @@ extern "C" {
  *           following call's uploads overlap them); synchronise down_stream, or make
  *           stream wait for it, before reading the host planes.
  * Consecutive calls on a handle may be enqueued without synchronising: a piece's upload
- * waits for the previous call's download of the same particles.  For this the handle
+ * waits for the previous call's download of the same particles.  Not for stream capture:
+ * the downloads end on down_stream, which stream does not join, and a call waits on
+ * events the previous call recorded.  For this the handle
  * keeps 3 nchunks + 1 CUDA events of the current device, created at the first call and
  * released by soax_destroy.  Both buffer sets must be bound.  Errors: SOAX_EINVAL (NULL
  * host pointer, bad nsteps, grid or nchunks), SOAX_ESCHEMA (flow fields), SOAX_ENOMEM
