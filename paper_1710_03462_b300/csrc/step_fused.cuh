@@ -12,6 +12,26 @@
 
 namespace soax {
 
+// The cell key of a particle whose position is held as turns T and stored as
+// x = turns_to_x(T), without waiting for x: with y = G T 2^-64 (G <= 1024), the stored
+// binary64 x (within 2^-53 relative of 2 pi T 2^-64, plus terms below 1e-24), c = RN(G/2pi)
+// and the rounding of x c give RN(x c) = y (1 + eta), |eta| <= 4.01 2^-53, i.e. within
+// 1024 * 4.01 * 2^-53 = 4.6e-13 of y.  So floor(RN(x c)) = floor(y) = floor(G T / 2^64)
+// (the high word of G T) unless frac(y), the low word, lies within 2^-40 of an integer
+// (T at the top of the turn, where x may wrap to 0, included); there cell_index of the
+// stored x decides.  Same bits as cell_key(x, y, z).
+__device__ __forceinline__ int cell_index_turns(uint64_t T, double x, const CellKeyK& k) {
+  const uint64_t lo = T * (uint64_t)k.G;
+  if (lo >= (1ull << 24) && lo <= 0ull - (1ull << 24)) return (int)__umul64hi(T, (uint64_t)k.G);
+  return min(cell_index(x, k.cfx, k.cm, k.ce), k.G - 1);
+}
+
+__device__ __forceinline__ uint32_t cell_key_turns(const uint64_t T[3], double x, double y, double z,
+                                                   const CellKeyK& k) {
+  const int ix = cell_index_turns(T[0], x, k), iy = cell_index_turns(T[1], y, k), iz = cell_index_turns(T[2], z, k);
+  return (uint32_t)((iz * k.G + iy) * k.G + ix);
+}
+
 // nsteps steps of one particle (the ragged tail of a launch).  Same per-particle
 // function as fused_group, so a particle gets the same bits on either path.
 template <bool TAU, bool ACC, class Trig>
@@ -28,7 +48,7 @@ __device__ __forceinline__ void fused_tail(const EnsArgs& e, const StepC& kc, co
     e.px[i] = x;
     e.py[i] = y;
     e.pz[i] = z;
-    if (keys) keys[i] = cell_key(x, y, z, ck);
+    if (keys) keys[i] = cell_key_turns(T, x, y, z, ck);
     e.vx[i] = v[0]; e.vy[i] = v[1]; e.vz[i] = v[2];
     if constexpr (ACC) { e.ax[i] = a[0]; e.ay[i] = a[1]; e.az[i] = a[2]; }
   }
@@ -113,7 +133,7 @@ __device__ __forceinline__ void fused_group(const EnsArgs& e, const StepC& kc, c
   store_f64<PPT, 128>(e.pz, i0, z);
   if (keys) {
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) keys[i0 + j] = cell_key(x[j], y[j], z[j], ck);
+    for (int j = 0; j < PPT; ++j) keys[i0 + j] = cell_key_turns(T[j], x[j], y[j], z[j], ck);
   }
   store_f32<PPT, 128>(e.vx, i0, vx);
   store_f32<PPT, 128>(e.vy, i0, vy);
@@ -241,7 +261,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused_gather(EnsArgs e
     eout.px[i] = x;
     eout.py[i] = y;
     eout.pz[i] = z;
-    if (keys) keys[i] = cell_key(x, y, z, ck);
+    if (keys) keys[i] = cell_key_turns(T, x, y, z, ck);
     eout.vx[i] = v[0]; eout.vy[i] = v[1]; eout.vz[i] = v[2];
     if constexpr (ACC) { eout.ax[i] = a[0]; eout.ay[i] = a[1]; eout.az[i] = a[2]; }
   }

@@ -366,3 +366,35 @@ def test_fused_full_size_wide_n64M_sampled():
     assert sk.min() >= 0 and sk.max() < grid ** 3
     del p, ws, keys, perm, ids_before, ids
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("G", [7, 32, 64, 1024])
+def test_fused_keys_at_cell_boundaries(G):
+    """The fused kernels take a particle's key from its turns except within 2^-40 of a cell
+    boundary, where the stored position decides.  Positions within a few ulps of every
+    boundary (and at 0 and just below 2pi), held still (zero flow and velocity), exercise
+    that fallback in the plain fused step, its ragged tail and the gather step: the keys
+    must be soax_cell_keys of the positions they store, bit for bit."""
+    c = G / sx.TWO_PI
+    base = np.arange(G + 1) / c
+    xs = [base, np.array([0.0, np.nextafter(sx.TWO_PI, 0.0), 1e-300])]
+    up, dn = base.copy(), base.copy()
+    for _ in range(4):
+        up = np.nextafter(up, np.inf)
+        dn = np.nextafter(dn, -np.inf)
+        xs += [up.copy(), dn.copy()]
+    x = np.concatenate(xs)
+    x = x[(x >= 0) & (x < sx.TWO_PI)]
+    rng = np.random.default_rng(G)
+    n = 3 * x.size + 5                      # a ragged tail
+    pos = [rng.choice(x, n) for _ in range(3)]
+    d = {"id": [np.arange(n, dtype=np.int32)], "pos": pos, "vel": [np.zeros(n, np.float32) for _ in range(3)]}
+    still = sx.Flow(A=0.0, B=0.0, C=0.0, tau=0.1, dt=1e-3)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    p.load(d)
+    keys = p.step_fused(still, 1, grid=G)
+    assert torch.equal(keys[:n], p.cell_keys(G))
+    assert np.array_equal(keys[:n].cpu().numpy().view(np.uint32), oracle.cell_keys(*p.numpy()["pos"], G))
+    ident = torch.arange(n, dtype=torch.int32, device=p.device)
+    keys = p.step_fused(still, 1, grid=G, perm=ident)
+    assert torch.equal(keys[:n], p.cell_keys(G))
