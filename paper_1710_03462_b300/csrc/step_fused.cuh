@@ -20,10 +20,16 @@ namespace soax {
 // (the high word of G T) unless frac(y), the low word, lies within 2^-40 of an integer
 // (T at the top of the turn, where x may wrap to 0, included); there cell_index of the
 // stored x decides.  Same bits as cell_key(x, y, z).
+// The exact path, out of line: it runs about once per 2^39 coordinates, and inlined at
+// every key site it made the plain fused step 1.9 % slower.
+static __device__ __noinline__ int cell_index_exact(double x, uint64_t cfx, uint64_t cm, int ce, int G) {
+  return min(cell_index(x, cfx, cm, ce), G - 1);
+}
+
 __device__ __forceinline__ int cell_index_turns(uint64_t T, double x, const CellKeyK& k) {
   const uint64_t lo = T * (uint64_t)k.G;
   if (lo >= (1ull << 24) && lo <= 0ull - (1ull << 24)) return (int)__umul64hi(T, (uint64_t)k.G);
-  return min(cell_index(x, k.cfx, k.cm, k.ce), k.G - 1);
+  return cell_index_exact(x, k.cfx, k.cm, k.ce, k.G);
 }
 
 __device__ __forceinline__ uint32_t cell_key_turns(const uint64_t T[3], double x, double y, double z,
@@ -231,7 +237,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_step_soa_fused_gather(EnsArgs e
       asm volatile("prefetch.global.L2 [%0];" ::"l"(ein.vy + pf));
       asm volatile("prefetch.global.L2 [%0];" ::"l"(ein.vz + pf));
     }
-    for (int p = 0; p < g.nother; ++p) {
+    // The copied planes; a 4-byte first one (an i32 id) without the per-plane size
+    // dispatch (21 fewer instructions per particle, 0.8 % of the launch).
+    int p0 = 0;
+    if (g.nother > 0 && g.es[0] == 4) {
+      static_cast<uint32_t*>(g.out[0])[i] = static_cast<const uint32_t*>(g.in[0])[src];
+      p0 = 1;
+    }
+    for (int p = p0; p < g.nother; ++p) {
       const int es = g.es[p];
       if (es == 8)
         static_cast<unsigned long long*>(g.out[p])[i] = static_cast<const unsigned long long*>(g.in[p])[src];
