@@ -78,6 +78,8 @@ def parse_args(argv=None):
                     help="run only this secondary row (profiling captures)")
     ap.add_argument("--n", type=int, default=None, help="particles (default: the row's workload)")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="pieces per soax_step_host call in the e2e loop")
+    ap.add_argument("--e2e-no-defer", action="store_true",
+                    help="e2e: each call downloads its own result (no interleaving with the next call's uploads)")
     ap.add_argument("--nens", type=int, default=None, help="--only batched: the first NENS ensembles")
     ap.add_argument("--fixed-tune", action="store_true", help="--only batched: a fixed launch shape, no autotuning")
     ap.add_argument("--nsteps", type=int, nargs="*", default=None,
@@ -351,7 +353,8 @@ def run_soax(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         p.step_host(host, flow, RK2_PER_STEP, WL["grid"], nchunks=args.e2e_chunks, ws=e2e_ws, stream=stream,
-                    up_stream=s_up, down_stream=s_dn)
+                    up_stream=s_up, down_stream=s_dn, defer=not args.e2e_no_defer)
+    p.step_host_finish(down_stream=s_dn)  # the last interval's downloads
     torch.cuda.synchronize(dev)
     e2e_el = time.perf_counter() - t0
     e2e_units, e2e_max = aggregate(n * RK2_PER_STEP * e2e_steps, e2e_el, dev)
@@ -382,7 +385,9 @@ def run_soax(args):
         "e2e": {"value": e2e_units / e2e_max, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d, "steps": e2e_steps,
                 "copies": f"soax_step_host, {args.e2e_chunks} pieces per call: piece uploads overlap the "
-                          "steps of the pieces already up, downloads overlap the next call's uploads",
+                          "steps of the pieces already up; " + ("each call's downloads overlap the next call's uploads"
+                          if args.e2e_no_defer else "each call's downloads are interleaved with the next call's "
+                          "uploads piece by piece (defer), the last call's by soax_step_host_finish"),
                 "link": link,
                 "floor": e2e_floor(n * RK2_PER_STEP, e2e_steps, statistics.mean(sort_ms) / 1e3, h2d, link)},
         "gpu_launches": args.steps * (1 + sort_launches),

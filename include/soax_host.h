@@ -43,6 +43,14 @@ extern "C" {
  *           has passed the call.
  *  fl, nsteps (>= 0), grid (1..1024): as for soax_step_fused_keys.
  *  nchunks: pieces (0 = 16); at most one piece per 16 particles is used.
+ *  defer:   0: the call enqueues its downloads.  1: it leaves them to the next
+ *           soax_step_host call on this handle, which enqueues each piece's download just
+ *           before its own upload of the same piece and holds it back until its upload
+ *           two pieces earlier has landed, so the two link directions move together
+ *           instead of the downloads running ahead; or to soax_step_host_finish.  Until
+ *           one of those has been enqueued, the live device planes must not be modified
+ *           or rebound (they are what will be downloaded), and the host planes of the
+ *           deferred call are final only once down_stream has passed it.
  *  ws:      soax_sort_workspace_bytes(h, grid) bytes (16-byte aligned): the keys and the
  *           permutation (soax_sort_results gives the permutation afterwards).
  *  stream, up_stream, down_stream: the steps, sort and gathers run on stream, the copies
@@ -60,9 +68,16 @@ extern "C" {
  * host pointer, bad nsteps, grid or nchunks), SOAX_ESCHEMA (flow fields), SOAX_ENOMEM
  * (workspace too small), SOAX_EALIGN, SOAX_EUNBOUND; all before any copy or launch.
  * SOAX_ECUDA if an event, copy or launch cannot be made (work enqueued before it
- * stays enqueued). */
+ * stays enqueued; a deferred call's downloads are then dropped).  Validation also
+ * rejects defer other than 0 or 1. */
 int soax_step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, int32_t grid, int32_t nchunks,
-                   void* ws, size_t ws_bytes, void* stream, void* up_stream, void* down_stream);
+                   int32_t defer, void* ws, size_t ws_bytes, void* stream, void* up_stream, void* down_stream);
+
+/* Enqueue, on down_stream, the downloads a soax_step_host call with defer = 1 left
+ * (nothing if none are pending); the host planes are final once down_stream has passed
+ * them.  SOAX_EINVAL for a NULL handle; SOAX_ECUDA if a copy cannot be enqueued (the
+ * deferred call's host planes are then undefined). */
+int soax_step_host_finish(soax_t h, void* down_stream);
 
 #ifdef __cplusplus
 }

@@ -199,7 +199,7 @@ class Particles:
         return out
 
     def step_host(self, host, f: Flow, nsteps, grid, nchunks=0, ws=None, stream=None, up_stream=None,
-                  down_stream=None):
+                  down_stream=None, defer=False):
         """soax_step_host: one sort interval of the set held in the host tensors `host`
         ({name: [comp0, ...]}, contiguous CPU tensors of the planes' element sizes and n
         elements, pinned for overlap): uploaded in nchunks pieces (0: the library's
@@ -207,8 +207,10 @@ class Particles:
         cell, gathered and downloaded back into `host`, all asynchronously: the host
         tensors are final once down_stream has passed the call (synchronise it or the
         device), the device planes once `stream` has.  Copies run on up_stream and
-        down_stream (two streams of this object when not given).  Returns the permutation
-        (int32 view into ws)."""
+        down_stream (two streams of this object when not given).  defer: leave the
+        downloads to the next step_host call (interleaved with its uploads) or to
+        step_host_finish; the live planes must not change meanwhile.  Returns the
+        permutation (int32 view into ws)."""
         ptrs = []
         for name, dt, nc, _ in self.schema:
             comps = host[name]
@@ -220,7 +222,18 @@ class Particles:
                 if t.element_size() != torch.empty(0, dtype=TORCH_DTYPES[dt]).element_size() or t.numel() < self.n:
                     raise ValueError(f"step_host: field {name} needs n elements of its size")
                 ptrs.append(t.data_ptr())
-        ws = self.sort_workspace(grid) if ws is None else ws
+        if ws is None:
+            # One workspace per grid, kept by this object: the call's keys and permutation
+            # live there until its device work has run, which can be long after the call
+            # returns (a workspace freed on return could be handed to other work while the
+            # call's sort still writes into it).
+            cache = self.__dict__.setdefault("_host_ws", {})
+            if grid not in cache:
+                cache[grid] = self.sort_workspace(grid)
+            ws = cache[grid]
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if s != torch.cuda.current_stream(self.device):
+            ws.record_stream(s)
         if up_stream is None or down_stream is None:
             if getattr(self, "_copy_streams", None) is None:
                 self._copy_streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
@@ -228,10 +241,19 @@ class Particles:
             down_stream = down_stream or self._copy_streams[1]
         arr = (C.c_void_p * max(len(ptrs), 1))(*ptrs)
         fl = self.flow(f)
-        _check(lib().soax_step_host(self.h, arr, C.byref(fl), int(nsteps), int(grid), int(nchunks), _ptr(ws),
-                                    ws.numel(), _stream(stream), _stream(up_stream), _stream(down_stream)),
+        _check(lib().soax_step_host(self.h, arr, C.byref(fl), int(nsteps), int(grid), int(nchunks), int(bool(defer)),
+                                    _ptr(ws), ws.numel(), _stream(stream), _stream(up_stream), _stream(down_stream)),
                "soax_step_host")
         return self.sort_results(grid, ws)[1]
+
+    def step_host_finish(self, down_stream=None):
+        """soax_step_host_finish: enqueue the downloads a step_host(defer=True) call left
+        (on down_stream, this object's download stream when not given)."""
+        if down_stream is None:
+            if getattr(self, "_copy_streams", None) is None:
+                self._copy_streams = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
+            down_stream = self._copy_streams[1]
+        _check(lib().soax_step_host_finish(self.h, _stream(down_stream)), "soax_step_host_finish")
 
     def numpy(self):
         """Live planes (the current size) as numpy arrays (synchronises)."""

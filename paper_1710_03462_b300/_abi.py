@@ -76,7 +76,8 @@ SIGNATURES = {
     "soax_step_batched": [_P(_p), _P(soax_flow), _i32, _i32, _P(soax_tune), _p, _sz, _p],
     "soax_autotune": [_P(_p), _P(soax_flow), _i32, _i32, _p, _sz, _P(soax_tune), _p],
     "soax_sync": [_p],
-    "soax_step_host": [_p, _P(_p), _P(soax_flow), _i32, _i32, _i32, _p, _sz, _p, _p, _p],
+    "soax_step_host": [_p, _P(_p), _P(soax_flow), _i32, _i32, _i32, _i32, _p, _sz, _p, _p, _p],
+    "soax_step_host_finish": [_p, _p],
 }
 EXPORTS = list(SIGNATURES)
 

@@ -11,6 +11,7 @@
 // upload of a piece waits for this call's download of the same particles (event down[c]):
 // the host buffer is the same, and so is the device range (the gather target is the
 // next call's live set).
+#include <algorithm>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -37,6 +38,13 @@ struct Pipe {
   std::vector<cudaEvent_t> up, gathered, down;
   std::vector<int64_t> lo, hi;  // the last call's pieces: [lo[c], hi[c])
   bool pending = false;         // that call's downloads may still be in flight
+  // A call made with defer leaves its downloads to the next call (interleaved with its
+  // uploads) or to soax_step_host_finish: where they go, where they come from, and how
+  // many of its pieces have been enqueued.
+  bool deferred = false;
+  std::vector<void*> dhost;
+  int dbuf = 0;
+  size_t ndone = 0;
 };
 
 std::mutex g_mu;
@@ -138,19 +146,47 @@ int wait(void* s, cudaEvent_t e) {
   return err == cudaSuccess ? SOAX_OK : cuda_fail(err, "soax_step_host: stream wait");
 }
 
+// The download of piece j of a deferred call: after its gather, into its host planes.
+int download_piece(soax_t h, Pipe& P, size_t j, void* down) {
+  const int64_t a = P.lo[j], cnt = P.hi[j] - P.lo[j];
+  if (int r = wait(down, P.gathered[j])) return r;
+  for (int p = 0; p < h->nplanes; ++p) {
+    const size_t es = (size_t)h->plane_esize[p];
+    if (int r = copy(static_cast<char*>(P.dhost[p]) + a * es, static_cast<const char*>(h->planes[P.dbuf][p]) + a * es,
+                     cnt * es, cudaMemcpyDeviceToHost, down))
+      return r;
+  }
+  return record(P.down[j], down);
+}
+
+// Enqueue what is left of a deferred call's downloads.
+int flush_deferred(soax_t h, Pipe& P, void* down) {
+  for (; P.ndone < P.lo.size(); ++P.ndone)
+    if (int r = download_piece(h, P, P.ndone, down)) return r;
+  P.deferred = false;
+  return SOAX_OK;
+}
+
 int step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, int32_t grid, int32_t nchunks,
-              void* ws, size_t ws_bytes, void* stream, void* up, void* down) {
+              int32_t defer, void* ws, size_t ws_bytes, void* stream, void* up, void* down) {
   const char* who = "soax_step_host";
   if (int r = check_handle(h)) return r;
   if (nsteps < 0) return fail(SOAX_EINVAL, std::string(who) + ": nsteps < 0");
   if (grid < 1 || grid > 1024) return fail(SOAX_EINVAL, std::string(who) + ": grid must be in 1..1024");
   if (nchunks < 0 || nchunks > kMaxChunks)
     return fail(SOAX_EINVAL, std::string(who) + ": nchunks must be in 0.." + std::to_string(kMaxChunks));
+  if (defer != 0 && defer != 1) return fail(SOAX_EINVAL, std::string(who) + ": defer must be 0 or 1");
   EnsArgs e;
   FlowK f;
   if (int r = make_ens_args(h, fl, h->current, &e, &f, who)) return r;
   const int64_t n = h->n;
   if (n == 0) {  // nothing moves; the live set flips as after soax_permute
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      auto it = g_pipes.find(h);
+      if (it != g_pipes.end() && it->second.deferred)
+        if (int r = flush_deferred(h, it->second, down)) return r;
+    }
     h->current ^= 1;
     return SOAX_OK;
   }
@@ -182,8 +218,15 @@ int step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, 
     P.lo.assign(P.down.size(), 0);
     P.hi.assign(P.down.size(), INT64_MAX);
     P.pending = true;
+    P.deferred = false;
     return r;
   };
+  // The previous call's deferred downloads interleave with this call's uploads only when
+  // both cut the set the same way; otherwise they are all enqueued first.
+  const bool interleave = P.deferred && P.lo.size() == (size_t)C &&
+                          std::equal(P.lo.begin(), P.lo.end(), cut.begin());
+  if (P.deferred && !interleave)
+    if (int r = flush_deferred(h, P, down)) return failed(r);
 
   // Work already on stream (e.g. the last use of these planes) comes first.
   if (int r = record(P.start, stream)) return failed(r);
@@ -192,6 +235,15 @@ int step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, 
   // 1. Upload and step piece by piece.
   for (int c = 0; c < C; ++c) {
     const int64_t a = cut[c], cnt = cut[c + 1] - cut[c];
+    if (interleave) {
+      // The previous call's download of this piece, held back until this call's upload
+      // two pieces earlier has landed: the two directions then move together, piece by
+      // piece, instead of the downloads running ahead and the uploads finishing alone.
+      if (c >= 2)
+        if (int r = wait(down, P.up[c - 2])) return failed(r);
+      if (int r = download_piece(h, P, (size_t)c, down)) return failed(r);
+      P.ndone = (size_t)c + 1;
+    }
     if (P.pending)
       for (size_t j = 0; j < P.lo.size(); ++j)
         if (P.lo[j] < a + cnt && a < P.hi[j])
@@ -211,28 +263,43 @@ int step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, 
   // 2. The permutation that sorts every key.
   if (int r = soax_sort_perm(h, grid, keys, ws, ws_bytes, stream)) return failed(r);
 
-  // 3. Gather and download piece by piece.
+  // 3. Gather piece by piece, and download each piece (now, or deferred).
+  P.lo.assign(cut.begin(), cut.end() - 1);
+  P.hi.assign(cut.begin() + 1, cut.end());
+  P.dhost.assign(host, host + h->nplanes);
+  P.dbuf = other;
+  P.ndone = 0;
+  P.deferred = false;
   for (int c = 0; c < C; ++c) {
-    const int64_t a = cut[c], cnt = cut[c + 1] - cut[c];
-    if (int r = permute_range(h, perm, a, cnt, stream)) return failed(r);
+    if (int r = permute_range(h, perm, cut[c], cut[c + 1] - cut[c], stream)) return failed(r);
     if (int r = record(P.gathered[c], stream)) return failed(r);
-    if (int r = wait(down, P.gathered[c])) return failed(r);
-    for (int p = 0; p < h->nplanes; ++p) {
-      const size_t es = (size_t)h->plane_esize[p];
-      if (int r = copy(static_cast<char*>(host[p]) + a * es, static_cast<const char*>(h->planes[other][p]) + a * es,
-                       cnt * es, cudaMemcpyDeviceToHost, down))
-        return failed(r);
+    if (!defer) {
+      if (int r = download_piece(h, P, (size_t)c, down)) return failed(r);
+      P.ndone = (size_t)c + 1;
     }
-    if (int r = record(P.down[c], down)) return failed(r);
   }
   // stream does not wait for the downloads: the next call's start event on stream must
   // not hold its uploads behind this call's downloads (they overlap them, piece by
-  // piece).  The host planes are final once down_stream has passed the call.
-
-  P.lo.assign(cut.begin(), cut.end() - 1);
-  P.hi.assign(cut.begin() + 1, cut.end());
+  // piece).  The host planes are final once down_stream has passed the call (with defer,
+  // the next call or soax_step_host_finish).
+  P.deferred = defer != 0;
   P.pending = true;
   h->current = other;
+  return SOAX_OK;
+}
+
+int step_host_finish(soax_t h, void* down) {
+  if (int r = check_handle(h)) return r;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_pipes.find(h);
+  if (it == g_pipes.end() || !it->second.deferred) return SOAX_OK;
+  Pipe& P = it->second;
+  if (int r = flush_deferred(h, P, down)) {
+    P.lo.assign(P.down.size(), 0);
+    P.hi.assign(P.down.size(), INT64_MAX);
+    P.deferred = false;
+    return r;
+  }
   return SOAX_OK;
 }
 
@@ -250,7 +317,9 @@ void release_host_pipe(const soax_s* h) {
 }  // namespace soax
 
 extern "C" int soax_step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, int32_t grid,
-                              int32_t nchunks, void* ws, size_t ws_bytes, void* stream, void* up_stream,
-                              void* down_stream) {
-  return soax::step_host(h, host, fl, nsteps, grid, nchunks, ws, ws_bytes, stream, up_stream, down_stream);
+                              int32_t nchunks, int32_t defer, void* ws, size_t ws_bytes, void* stream,
+                              void* up_stream, void* down_stream) {
+  return soax::step_host(h, host, fl, nsteps, grid, nchunks, defer, ws, ws_bytes, stream, up_stream, down_stream);
 }
+
+extern "C" int soax_step_host_finish(soax_t h, void* down_stream) { return soax::step_host_finish(h, down_stream); }

@@ -140,7 +140,7 @@ def test_step_host_validation_without_gpu():
     fl = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 1, 2, -1)
     bad = _abi.soax_flow(1, 1, 1, 0.1, 1e-3, 0.0, -1, 2, 1, -1)  # pos/vel swapped
     rc, h0 = _create(sx.BASIC_SCHEMA, 100)
-    assert L.soax_step_host(h0, (C.c_void_p * 7)(*([0x1000] * 7)), C.byref(fl), 10, 32, 0, C.c_void_p(0x10000),
+    assert L.soax_step_host(h0, (C.c_void_p * 7)(*([0x1000] * 7)), C.byref(fl), 10, 32, 0, 0, C.c_void_p(0x10000),
                             1 << 30, None, None, None) == -8    # planes not bound
     L.soax_destroy(h0)
     rc, h = _create(sx.BASIC_SCHEMA, 100)
@@ -150,28 +150,32 @@ def test_step_host_validation_without_gpu():
                 assert L.soax_bind(h, f, c, b, C.c_void_p(0x100000 * (1 + 8 * f + 2 * c + b))) == 0
     host = (C.c_void_p * 7)(*([0x1000] * 7))
     ws = C.c_void_p(0x10000)
-    args = lambda **k: dict(dict(host=host, fl=C.byref(fl), nsteps=10, grid=32, nchunks=0, ws=ws, wsb=1 << 30), **k)
+    args = lambda **k: dict(dict(host=host, fl=C.byref(fl), nsteps=10, grid=32, nchunks=0, defer=0, ws=ws,
+                                 wsb=1 << 30), **k)
 
     def call(**k):
         a = args(**k)
-        return L.soax_step_host(h, a["host"], a["fl"], a["nsteps"], a["grid"], a["nchunks"], a["ws"], a["wsb"],
-                                None, None, None)
+        return L.soax_step_host(h, a["host"], a["fl"], a["nsteps"], a["grid"], a["nchunks"], a.get("defer", 0),
+                                a["ws"], a["wsb"], None, None, None)
     assert call(nsteps=-1) == -1
     assert call(grid=0) == -1 and call(grid=1025) == -1
     assert call(nchunks=-1) == -1 and call(nchunks=1025) == -1
     assert b"nchunks" in L.soax_last_error()
+    assert call(defer=2) == -1 and b"defer" in L.soax_last_error()
     assert call(fl=C.byref(bad)) == -2
     assert call(host=None) == -1
     holes = (C.c_void_p * 7)(*([0x1000] * 6 + [0]))
     assert call(host=holes) == -1 and b"host plane 6" in L.soax_last_error()
     assert call(wsb=16) == -6
     assert call(ws=C.c_void_p(0x10008)) == -3
-    assert L.soax_step_host(None, host, C.byref(fl), 1, 32, 0, ws, 1 << 30, None, None, None) == -1
+    assert L.soax_step_host(None, host, C.byref(fl), 1, 32, 0, 0, ws, 1 << 30, None, None, None) == -1
+    assert L.soax_step_host_finish(None, None) == -1
+    assert L.soax_step_host_finish(h, None) == 0                 # nothing deferred: no work
     L.soax_destroy(h)
     # An empty set moves nothing: the live set flips, as after soax_permute.
     rc, h = _create(sx.BASIC_SCHEMA, 0)
     cur = C.c_int32()
-    assert L.soax_step_host(h, None, C.byref(fl), 10, 32, 0, None, 0, None, None, None) == 0
+    assert L.soax_step_host(h, None, C.byref(fl), 10, 32, 0, 1, None, 0, None, None, None) == 0
     assert L.soax_current(h, C.byref(cur)) == 0 and cur.value == 1
     L.soax_destroy(h)
 

@@ -166,3 +166,66 @@ def test_agrees_with_the_oracle():
         assert np.all(np.minimum(dx, sx.TWO_PI - dx) <= 1e-11), c
         assert np.allclose(host["vel"][c].numpy()[inv], ovel[c], rtol=1e-5, atol=1e-9), c
     assert np.array_equal(host["id"][0].numpy(), d["id"][0][perm])
+
+
+@pytest.mark.parametrize("pieces", [(16, 16, 16), (8, 3, 13), (5, 5, 1)])
+def test_deferred_downloads_chain(pieces):
+    # Each call leaves its downloads to the next (interleaved with its uploads when the
+    # pieces match, all enqueued first when they do not); finish enqueues the last ones.
+    n = 150001
+    d = soax_inputs.basic_set(n, 21)
+    ref = sx.Particles(sx.BASIC_SCHEMA, n)
+    ref.load(d)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    host = _host(d)
+    s = torch.cuda.Stream()
+    for k in pieces:
+        p.step_host(host, FLOW, 10, GRID, nchunks=k, stream=s, defer=True)
+        _device_interval(ref, FLOW, 10, GRID)
+    p.step_host_finish()
+    torch.cuda.synchronize()
+    _same(host, ref)
+    _same(host, p)
+
+
+def test_deferred_then_immediate_and_finish_twice():
+    n = 40007
+    d = soax_inputs.basic_set(n, 22)
+    ref = sx.Particles(sx.BASIC_SCHEMA, n)
+    ref.load(d)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    host = _host(d)
+    p.step_host(host, FLOW, 10, GRID, nchunks=4, defer=True)
+    p.step_host(host, FLOW, 10, GRID, nchunks=4)           # downloads the first, then its own
+    _device_interval(ref, FLOW, 10, GRID)
+    _device_interval(ref, FLOW, 10, GRID)
+    p.step_host_finish()                                     # nothing pending: no work
+    p.step_host_finish()
+    torch.cuda.synchronize()
+    _same(host, ref)
+
+
+def test_deferred_into_other_host_buffers():
+    # A deferred call's result goes to its own host planes even when the next call
+    # streams from another set of host planes.
+    n = 30000
+    d = soax_inputs.basic_set(n, 23)
+    ref = sx.Particles(sx.BASIC_SCHEMA, n)
+    ref.load(d)
+    _device_interval(ref, FLOW, 10, GRID)
+    first = ref.numpy()
+    _device_interval(ref, FLOW, 10, GRID)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    h1, h2 = _host(d), _host(d)
+    p.step_host(h1, FLOW, 10, GRID, nchunks=6, defer=True)
+    torch.cuda.synchronize()
+    for k in h2:                                            # h2 holds the first result
+        for c, t in enumerate(h2[k]):
+            t.copy_(torch.from_numpy(first[k][c]))
+    p.step_host(h2, FLOW, 10, GRID, nchunks=6, defer=True)
+    p.step_host_finish()
+    torch.cuda.synchronize()
+    for k in h1:
+        for c, t in enumerate(h1[k]):
+            assert t.numpy().tobytes() == first[k][c].tobytes(), (k, c)
+    _same(h2, ref)
