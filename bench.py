@@ -74,7 +74,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="soax", choices=["soax", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
-    ap.add_argument("--only", choices=["euler", "adjoint", "batched", "aos", "fixed"],
+    ap.add_argument("--only", choices=["euler", "adjoint", "batched", "aos", "fixed", "plain", "wide"],
                     help="run only this secondary row (profiling captures)")
     ap.add_argument("--n", type=int, default=None, help="particles (default: the row's workload)")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="pieces per soax_step_host call in the e2e loop")
@@ -82,6 +82,7 @@ def parse_args(argv=None):
                     help="e2e: each call downloads its own result (no interleaving with the next call's uploads)")
     ap.add_argument("--nens", type=int, default=None, help="--only batched: the first NENS ensembles")
     ap.add_argument("--fixed-tune", action="store_true", help="--only batched: a fixed launch shape, no autotuning")
+    ap.add_argument("--intervals", type=int, default=None, help="--only wide: sort intervals to time")
     ap.add_argument("--nsteps", type=int, nargs="*", default=None,
                     help="--only fixed: steps per launch (default 10 and 20)")
     return ap.parse_args(argv)
@@ -217,66 +218,146 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------------------- oracle timing
+def oracle_interval(oracle, st, wl, threads, aos=False):
+    """One sort interval of the oracle on the sample st (in place): sort_every RK2 steps,
+    the cell keys, the stable argsort and the permute of every plane.  st holds "planes"
+    (id, pos[3], vel[3], and for the wide record acc[3], mass, tag) or, with aos, "rec"
+    (the natural AoS records) plus the layout to step them."""
+    steps = wl["sort_every"]
+    tau_scale = wl.get("tau_scale", 0.0)
+    if aos:
+        L = st["layout"]
+        oracle.step_aos(st["rec"], L["rb"], L["pos"], L["vel"], wl["A"], wl["B"], wl["C"], wl.get("tau", 0.0),
+                        wl["dt"], steps, acc_off=L.get("acc", -1), mass_off=L.get("mass", -1), tau_scale=tau_scale,
+                        threads=threads)
+        return
+    pl = st["planes"]
+    pos, vel = pl["pos"], pl["vel"]
+    oracle.step_soa(pos, vel, wl["A"], wl["B"], wl["C"], wl.get("tau", 0.0), wl["dt"], steps, acc=pl.get("acc"),
+                    mass=pl["mass"][0] if "mass" in pl else None, tau_scale=tau_scale, threads=threads)
+    keys = oracle.cell_keys(*pos, wl["grid"])
+    perm, _ = oracle.stable_argsort(keys)
+    names = list(pl)
+    flat = [a for k in names for a in pl[k]]
+    out = oracle.permute(flat, perm)
+    k = 0
+    for name in names:
+        m = len(pl[name])
+        pl[name] = out[k:k + m]
+        k += m
+
+
+def oracle_sample(name, ns, aos=False):
+    """The first ns particles of a workload's set (seeded as the GPU run's), as oracle
+    planes or as AoS records."""
+    wl = soax_inputs.WORKLOADS[name]
+    d = soax_inputs.wide_set(ns, wl["seed"]) if name == "wide_n64M" else soax_inputs.basic_set(ns, wl["seed"])
+    planes = {k: [a.copy() for a in v] for k, v in d.items()}
+    if not aos:
+        return {"planes": planes}
+    import oracle
+    eb = {"i32": 4, "i64": 8, "u8": 1, "f32": 4, "f64": 8}
+    schema = WIDE_FIELDS if name == "wide_n64M" else BASIC_FIELDS
+    rb, offs = oracle.aos_layout([eb[t] for _, t, _ in schema], [c for _, _, c in schema])
+    rec = oracle.soa_to_aos([a for f, _, _ in schema for a in planes[f]], [eb[t] for _, t, _ in schema],
+                            [c for _, _, c in schema])
+    layout = {"rb": rb}
+    for (f, _, _), o in zip(schema, offs):
+        layout[f] = o
+    return {"rec": rec, "layout": layout}
+
+
+BASIC_FIELDS = [("id", "i32", 1), ("pos", "f64", 3), ("vel", "f32", 3)]
+WIDE_FIELDS = [("id", "i64", 1), ("pos", "f64", 3), ("vel", "f32", 3), ("acc", "f32", 3), ("mass", "f32", 1),
+               ("tag", "u8", 1)]
+
+
+def time_oracle(name, ns, threads, reps=1, warmup=1, aos=False, sort=True):
+    """Seconds per sort interval of the oracle (mean of reps after warmup untimed ones)
+    on ns particles of the workload with `threads` threads; the sample is drawn before
+    and the warm-up runs on it, so neither page faults on fresh arrays nor thread start-up
+    land in the timed region."""
+    import oracle
+    wl = dict(soax_inputs.WORKLOADS[name])
+    wl.setdefault("sort_every", wl.get("steps"))
+    st = oracle_sample(name, ns, aos=aos)
+    if not sort:
+        wl["grid"] = None
+
+    def one():
+        if sort:
+            oracle_interval(oracle, st, wl, threads, aos=aos)
+        elif aos:
+            oracle_interval(oracle, st, wl, threads, aos=True)
+        else:
+            pl = st["planes"]
+            oracle.step_soa(pl["pos"], pl["vel"], wl["A"], wl["B"], wl["C"], wl.get("tau", 0.0), wl["dt"],
+                            wl["sort_every"], acc=pl.get("acc"), mass=pl["mass"][0] if "mass" in pl else None,
+                            tau_scale=wl.get("tau_scale", 0.0), threads=threads)
+    for _ in range(warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        one()
+    return (time.perf_counter() - t0) / reps
+
+
+def oracle_baseline(name, n, reps=1, warmup=1, single_core=True, aos=True, sort=True):
+    """The oracle timed on the host cores on a bounded sample of a workload: all cores
+    (the reported value: SoA planes, RK2 steps of one sort interval plus its cell sort),
+    one core on a smaller sample, and the AoS records on all cores (steps only: the AoS
+    form has no sort here).  Returns the cpu_baseline object."""
+    cores = os.cpu_count() or 1
+    wl = soax_inputs.WORKLOADS[name]
+    steps = wl.get("sort_every", wl.get("steps"))
+    ns = min(n, 1 << 22)
+    el = time_oracle(name, ns, cores, reps=reps, warmup=warmup, sort=sort)
+    out = {"value": ns * steps / el, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+           "sample": f"{ns} of {n} particles x {steps} RK2 steps" + (" + one cell sort" if sort else "") +
+                     f" per timed interval, {reps} timed after {warmup} warm-up, SoA planes, {cores} threads "
+                     f"({el:.2f} s per interval)"}
+    if single_core:
+        n1 = max(1024, ns // max(cores, 1))
+        e1 = time_oracle(name, n1, 1, reps=1, warmup=1, sort=sort)
+        out["single_core"] = {"value": n1 * steps / e1, "unit": "particle-steps/s", "cores": 1,
+                              "sample": f"{n1} particles, same interval, 1 thread ({e1:.2f} s)"}
+    if aos:
+        ea = time_oracle(name, ns, cores, reps=1, warmup=1, aos=True, sort=False)
+        out["aos"] = {"value": ns * steps / ea, "unit": "particle-steps/s", "cores": cores,
+                      "sample": f"{ns} AoS records x {steps} RK2 steps, {cores} threads ({ea:.2f} s)"}
+        es = time_oracle(name, ns, cores, reps=1, warmup=1, sort=False)
+        out["soa_steps_only"] = {"value": ns * steps / es, "unit": "particle-steps/s", "cores": cores,
+                                 "sample": f"{ns} particles x {steps} RK2 steps, no sort ({es:.2f} s)"}
+    return out
+
+
 # ---------------------------------------------------------------------------- reference arm
 def run_reference(args):
     """The CPU oracle as the reference arm: each bench step is a bounded sample of the
-    workload (a quarter of the particles: 10 RK2 steps + the cell sort of that sample)."""
+    workload (a quarter of the particles: 10 RK2 steps + the cell sort of that sample),
+    timed by the same procedure as the GPU arm's cpu_baseline (oracle_baseline)."""
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    import oracle
-    cores = os.cpu_count() or 1
-    ns = min(args.n, 1 << 22)
-    d = soax_inputs.basic_set(ns, WL["seed"])
-    pos = [p.copy() for p in d["pos"]]
-    vel = [v.copy() for v in d["vel"]]
-    ids = d["id"][0].copy()
-
-    def one():
-        nonlocal pos, vel, ids
-        oracle.step_soa(pos, vel, WL["A"], WL["B"], WL["C"], WL["tau"], WL["dt"], RK2_PER_STEP, threads=cores)
-        keys = oracle.cell_keys(*pos, WL["grid"])
-        perm, _ = oracle.stable_argsort(keys)
-        out = oracle.permute([ids] + pos + vel, perm)
-        ids, pos, vel = out[0], out[1:4], out[4:7]
-
     steps = max(1, min(args.steps, 5))
-    for _ in range(max(0, min(args.warmup, 1))):
-        one()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        one()
-    el = time.perf_counter() - t0
-    value = ns * RK2_PER_STEP * steps / el
-    sample = f"{ns} of {args.n} particles x {RK2_PER_STEP} RK2 steps + cell sort, {steps} steps"
+    warm = max(1, min(args.warmup, 2))
+    base = oracle_baseline("sorted_n16M", args.n, reps=steps, warmup=warm)
+    value = base["value"]
+    ms = WL["sort_every"] * min(args.n, 1 << 22) / value * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
-            "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": el / steps * 1e3, "higher_is_better": True,
+            "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "sorted_n16M", "n": args.n, "grid": WL["grid"], "sort_every": RK2_PER_STEP},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": base,
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 def cpu_baseline(n):
-    """The oracle on the host cores: 10 RK2 steps + one cell sort over a bounded sample."""
-    import oracle
-    cores = os.cpu_count() or 1
-    ns = min(n, 1 << 22)
-    d = soax_inputs.basic_set(ns, WL["seed"])
-    pos = [p.copy() for p in d["pos"]]
-    vel = [v.copy() for v in d["vel"]]
-    t0 = time.perf_counter()
-    oracle.step_soa(pos, vel, WL["A"], WL["B"], WL["C"], WL["tau"], WL["dt"], RK2_PER_STEP, threads=cores)
-    keys = oracle.cell_keys(*pos, WL["grid"])
-    perm, _ = oracle.stable_argsort(keys)
-    oracle.permute(d["id"] + pos + vel, perm)
-    el = time.perf_counter() - t0
-    return {"value": ns * RK2_PER_STEP / el, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{ns} particles x {RK2_PER_STEP} RK2 steps + one cell sort (one bench step on a quarter "
-                      f"of the set), {el:.1f} s"}
+    """The oracle on the host cores (oracle_baseline on the bench workload)."""
+    return oracle_baseline("sorted_n16M", n)
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -368,6 +449,10 @@ def run_soax(args):
     fused_s = statistics.mean(fused_ms) / 1e3
     roofline = alu_roofline(torch, dev, STEP_KERNEL, n * RK2_PER_STEP, fused_s)
     roofline["hbm_GB/s"] = STEP_LAUNCH_BYTES * n / fused_s / 1e9
+    # Algorithmic fractions beside the issue rate: the plain step's 72 B per particle-step
+    # at this speed against the copy peak, and the FP32 work against the FP32 pipes.
+    roofline["hbm_equivalent"] = hbm_equivalent(BYTES_PER_PARTICLE_STEP, n * RK2_PER_STEP, fused_s)
+    roofline["fp32"] = fp32_fraction(torch, dev, STEP_KERNEL, n * RK2_PER_STEP, fused_s)
     sort_launches = 3 * 2  # (upsweep, scan, downsweep) x 2 passes; keys and permute-gather ride on the step
     line = {
         "metric": METRIC, "value": tot_units / max_el, "unit": "particle-steps/s", "n_gpus": world,
@@ -519,6 +604,30 @@ def hbm_roofline(bytes_per_unit, units, seconds, kernel=None):
             "traffic": ncu_traffic(kernel) if kernel else None, "kernel": kernel}
 
 
+def hbm_equivalent(bytes_per_unit, units, seconds):
+    """The rate a kernel that is not HBM-bound would need from HBM to do the same work in
+    one pass per step (the plain step's algorithmic bytes per particle-step), against the
+    copy peak: the algorithmic fraction beside an issue-rate roofline."""
+    peak, kind = measured_peaks()
+    achieved = bytes_per_unit * units / seconds / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": f"{kind} copy", "bytes_per_unit": bytes_per_unit}
+
+
+def fp32_fraction(torch, dev, kernel, units, seconds):
+    """FP32 lane operations per particle-step that ncu counted for the current sources
+    (FADD + FMUL + FFMA thread instructions, each packed FP32x2 instruction counted as two)
+    x units / time, against the FP32 pipes' peak: 128 FP32 lanes per SM per clock x SMs at
+    the maximum SM clock.  None figures when no record matches the sources."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * MAX_SM_MHZ * 1e6 / 1e12
+    rec = ncu_record(kernel)
+    ops = float(rec["fp32_ops_per_particle_step"]) if rec and "fp32_ops_per_particle_step" in rec else None
+    achieved = ops * units / seconds / 1e12 if ops else None
+    return {"achieved": achieved, "peak": peak, "unit": "T FP32 lane-ops/s", "frac": achieved / peak if achieved else None,
+            "ops_per_unit": ops, "peak_kind": f"128 FP32 lanes/SM/clock x {sms} SMs at {MAX_SM_MHZ:.0f} MHz"}
+
+
 def alu_roofline(torch, dev, kernel, units, seconds):
     """Roofline entry of an issue-bound launch: the thread-instructions per unit that ncu
     counted for the current sources x units / time, against the issue-rate peak.  None
@@ -639,40 +748,161 @@ def row_batched(sx, torch, dev, nens=None, fixed_tune=False):
         parts.append(q)
         flows.append(sx.Flow(A=abc[e, 0], B=abc[e, 1], C=abc[e, 2], tau=tau, dt=wb["dt"]))
     total = int(sizes[:nens].sum())
-    nst = 5
+    nst = wb["steps"]  # the workload's 200 steps for every form
     stream = torch.cuda.current_stream(dev)
-    # One persistent launch per step (autotuned), over nst steps.
+    # One persistent launch per step (autotuned), over the workload's steps.
     tune = sx.Tune(2, 512, 128, 0) if fixed_tune else sx.autotune(parts, flows, nsteps_probe=1)
     wsb = sx.step_batched(parts, flows, 1, tune)
-    t_b = _time(torch, lambda: sx.step_batched(parts, flows, nst, tune, ws=wsb))
-    # The workload's form: all its steps in ONE fused persistent launch (autotuned).
+    t_b = _events(torch, stream, lambda: sx.step_batched(parts, flows, nst, tune, ws=wsb))
+    # The workload's form: all its steps in ONE fused persistent launch (autotuned), called
+    # directly and replayed from a CUDA graph.
     tf = sx.Tune(2, 512, 128, 1) if fixed_tune else sx.autotune(parts, flows, nsteps_probe=10, fuse=True)
     wsf = sx.batched_workspace(parts)
     sx.step_batched(parts, flows, 1, tf, ws=wsf)
     kf = wb["steps"]
     t_f = _events(torch, stream, lambda: sx.step_batched(parts, flows, kf, tf, ws=wsf))
-    # Baseline: separate plain launches per step, captured in one CUDA graph.
+    sx.step_batched(parts, flows, kf, tf, ws=wsf)  # the plan for these arguments is in place before capture
+    torch.cuda.synchronize(dev)
+    g_f = _graph(torch, dev, lambda s: sx.step_batched(parts, flows, kf, tf, ws=wsf, stream=s))
+    t_fg = _events(torch, stream, g_f.replay)
+    # Baseline: separate plain launches per step, one CUDA graph per step of all ensembles.
+    g = _graph(torch, dev, lambda s: [q.step(f, 1, stream=s) for q, f in zip(parts, flows)])
+    t_plain_b = _events(torch, stream, lambda: [g.replay() for _ in range(nst)])
+    out = {"ensembles": len(parts), "particles": total,
+           "persistent": {"steps": nst, "launches": nst, "tune": tune.__dict__, "ms": t_b * 1e3,
+                          "particle-steps/s": total * nst / t_b,
+                          "roofline": hbm_roofline(BYTES_PER_PARTICLE_STEP, total * nst, t_b, "k_step_batched")},
+           "fused": {"steps": kf, "launches": 1, "tune": tf.__dict__, "ms": t_f * 1e3,
+                     "particle-steps/s": total * kf / t_f,
+                     "roofline": alu_roofline(torch, dev, "k_step_batched_fused", total * kf, t_f)},
+           "fused_graph": {"steps": kf, "launches": 1, "ms": t_fg * 1e3, "particle-steps/s": total * kf / t_fg,
+                           "how": "the fused launch captured in a CUDA graph and replayed"},
+           "plain_launches": {"launches_per_step": len(parts), "steps": nst, "ms": t_plain_b * 1e3,
+                              "particle-steps/s": total * nst / t_plain_b},
+           "persistent_over_plain": t_plain_b / t_b,
+           "fused_over_plain": (t_plain_b / nst) / (t_f / kf),
+           "fused_graph_over_plain": (t_plain_b / nst) / (t_fg / kf)}
+    del parts, g, g_f
+    torch.cuda.empty_cache()
+    return out
+
+
+def _graph(torch, dev, fn):
+    """fn captured in a CUDA graph on a side stream; returns the graph."""
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
         with torch.cuda.graph(g, stream=s):
-            for q, f in zip(parts, flows):
-                q.step(f, 1, stream=s)
+            fn(s)
     torch.cuda.current_stream(dev).wait_stream(s)
-    t_plain_b = _time(torch, lambda: [g.replay() for _ in range(nst)])
-    out = {"ensembles": len(parts), "particles": total,
-           "persistent": {"steps": nst, "tune": tune.__dict__, "particle-steps/s": total * nst / t_b,
-                          "roofline": hbm_roofline(BYTES_PER_PARTICLE_STEP, total * nst, t_b, "k_step_batched")},
-           "fused": {"steps": kf, "launches": 1, "tune": tf.__dict__, "ms": t_f * 1e3,
-                     "particle-steps/s": total * kf / t_f,
-                     "roofline": alu_roofline(torch, dev, "k_step_batched_fused", total * kf, t_f)},
-           "plain_launches": {"launches_per_step": len(parts), "steps": nst,
-                              "particle-steps/s": total * nst / t_plain_b},
-           "persistent_over_plain": t_plain_b / t_b,
-           "fused_over_plain": (t_plain_b / nst) / (t_f / kf)}
-    del parts, g
+    return g
+
+
+def row_plain_n65536(sx, torch, dev):
+    """The 65,536-particle set, 100 RK2 steps, SoA and AoS, on the device (2.5 MiB of
+    planes: L2-resident, so an HBM fraction means nothing here and the one-pass forms are
+    launch-bound; the 100 launches are captured in one CUDA graph).  Forms: 100 one-pass
+    SoA launches, the 100 steps in one fused launch, 100 AoS launches on the 48-B records;
+    the oracle runs the full 100 steps beside them (SoA and AoS, all cores and one)."""
+    w = soax_inputs.WORKLOADS["plain_n65536"]
+    n, K = w["n"], w["steps"]
+    d = soax_inputs.basic_set(n, w["seed"])
+    flow = sx.Flow(A=w["A"], B=w["B"], C=w["C"], tau=w["tau"], dt=w["dt"])
+    p = sx.Particles(sx.BASIC_SCHEMA, n, device=dev, shadow=False)
+    p.load(d)
+    aos = p.to_aos()
+    stream = torch.cuda.current_stream(dev)
+    g_soa = _graph(torch, dev, lambda s: p.step(flow, K, stream=s))
+    g_aos = _graph(torch, dev, lambda s: p.step_aos(aos, flow, K, stream=s))
+    t_soa = _events(torch, stream, g_soa.replay, reps=5)
+    t_fused = _events(torch, stream, lambda: p.step_fused(flow, K), reps=5)
+    t_aos = _events(torch, stream, g_aos.replay, reps=5)
+    units = n * K
+    out = {"n": n, "steps": K, "l2_resident": True,
+           "note": "2.5 MiB of planes stay in the 126 MB L2: HBM fractions are not meaningful; one-pass forms are "
+                   "bound by launch and per-step latency (100 launches in one CUDA graph)",
+           "soa_one_pass_graph": {"ms": t_soa * 1e3, "particle-steps/s": units / t_soa,
+                                  "launches": K, "hbm_equivalent_GB/s": 72 * units / t_soa / 1e9},
+           "soa_fused_one_launch": {"ms": t_fused * 1e3, "particle-steps/s": units / t_fused, "launches": 1},
+           "aos_one_pass_graph": {"ms": t_aos * 1e3, "particle-steps/s": units / t_aos, "launches": K},
+           "soa_over_aos": t_aos / t_soa, "fused_over_one_pass": t_soa / t_fused}
+    out["roofline"] = alu_roofline(torch, dev, "k_step_soa", units, t_soa)
+    out["roofline"]["note"] = "one-pass kernel's ncu instruction count at its 16.7M-particle capture"
+    out["cpu_baseline"] = oracle_baseline("plain_n65536", n, sort=False)
+    del p, aos, g_soa, g_aos
     torch.cuda.empty_cache()
+    return out
+
+
+def row_wide_n64M(sx, torch, dev, n=None, intervals=None):
+    """The wide record at its full size: 67,108,864 particles {i64 id, f64 pos[3], f32
+    vel[3], f32 acc[3], f32 mass, u8 tag}, tau = 0.1 mass, dt = 5e-4, acc written, 200 RK2
+    steps with a cell sort on the 64^3 grid every 20: each interval is one fused launch of
+    20 steps that gathers every plane through the previous sort's permutation and writes
+    the new 18-bit keys, then the stable radix sort of those keys (2 passes).  Also: the
+    one-pass step (88 algorithmic bytes per particle-step), the 64-B record AoS <-> SoA
+    round trip, and the oracle on a sample."""
+    w = soax_inputs.WORKLOADS["wide_n64M"]
+    n = w["n"] if n is None else n
+    every, grid = w["sort_every"], w["grid"]
+    nint = w["steps"] // every if intervals is None else intervals
+    d = soax_inputs.wide_set(n, w["seed"])
+    p = sx.Particles(sx.WIDE_SCHEMA, n, device=dev)
+    p.load(d)
+    del d
+    flow = sx.Flow(A=w["A"], B=w["B"], C=w["C"], tau=0.0, dt=w["dt"], tau_field="mass",
+                   tau_scale=w["tau_scale"], acc="acc")
+    ws = p.sort_workspace(grid)
+    keys = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    pending = {"perm": None}
+
+    def interval(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        p.step_fused(flow, every, grid=grid, keys=keys, perm=pending["perm"])
+        if ev is not None:
+            ev[1].record(stream)
+        pending["perm"] = p.sort_perm(grid, keys, ws)[1]
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(2):
+        interval()
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nint)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(nint):
+        interval(evs[k])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    total = e0.elapsed_time(e1) / 1e3
+    fused = statistics.mean(ev[0].elapsed_time(ev[1]) for ev in evs) / 1e3
+    srt = statistics.mean(ev[1].elapsed_time(ev[2]) for ev in evs) / 1e3
+    units = n * every * nint
+    out = {"workload": "wide_n64M", "n": n, "rk2_steps": every * nint, "sort_every": every, "grid": grid,
+           "fields": "i64 id, f64 pos[3], f32 vel[3], f32 acc[3], f32 mass, u8 tag",
+           "flow": "ABC A=B=C=1, tau = 0.1 mass, dt = 5e-4, acc written",
+           "ms": total * 1e3, "particle-steps/s": units / total, "interval_ms": total / nint * 1e3,
+           "fused_launch_ms": fused * 1e3, "sort_ms": srt * 1e3,
+           "l2": f"inputs larger than L2 ({n * 61 / 2**20:.0f} MiB of planes)"}
+    rl = alu_roofline(torch, dev, "k_step_soa_fused_gather/wide", n * every, fused)
+    rl["hbm_equivalent"] = hbm_equivalent(88, n * every, fused)
+    out["roofline"] = rl
+    # H1 as the workload states it: one pass over the planes per step.
+    t1 = _time(torch, lambda: p.step(flow, 1), reps=5)
+    out["step_one_pass"] = {"launch_ms": t1 * 1e3, "particle-steps/s": n / t1,
+                            "roofline": hbm_roofline(88, n, t1, "k_step_soa/wide")}
+    # The 64-B record round trip: SoA -> AoS reads 61 B of planes and writes 64 B, and back.
+    aos = p.to_aos()
+    t_rt = _time(torch, lambda: (p.to_aos(aos), p.from_aos(aos)), reps=3)
+    out["aos_soa_roundtrip"] = {"ms": t_rt * 1e3, "bytes_per_particle": 250,
+                                "roofline": hbm_roofline(250, n, t_rt, None)}
+    del aos, p, ws, keys
+    torch.cuda.empty_cache()
+    out["cpu_baseline"] = oracle_baseline("wide_n64M", n)
     return out
 
 
@@ -712,6 +942,8 @@ def secondary_rows(sx, torch, p, d, dev):
     rows["aos_soa_roundtrip"], rows["aos_step"] = row_aos(sx, torch, p, flow)
     rows["fwd_adjoint"] = row_adjoint(sx, torch, dev)
     rows["batched"] = row_batched(sx, torch, dev)
+    rows["plain_n65536"] = row_plain_n65536(sx, torch, dev)
+    rows["wide_n64M"] = row_wide_n64M(sx, torch, dev)
     return rows
 
 
@@ -726,6 +958,10 @@ def run_only(args):
         row = row_adjoint(sx, torch, dev, args.n)
     elif args.only == "batched":
         row = row_batched(sx, torch, dev, args.nens, args.fixed_tune)
+    elif args.only == "plain":
+        row = row_plain_n65536(sx, torch, dev)
+    elif args.only == "wide":
+        row = row_wide_n64M(sx, torch, dev, args.n, args.intervals)
     elif args.only == "fixed":
         row = row_fixed(sx, torch, dev, args.n or WL["n"], args.nsteps or [RK2_PER_STEP, 2 * RK2_PER_STEP])
     else:

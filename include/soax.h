@@ -182,7 +182,12 @@ int soax_remove(soax_t h, const uint32_t* idx, int64_t k, void* ws, size_t ws_by
  *   a1 = (u(x) - v)/tau,  xm = x + dt/2 v,  vm = v + dt/2 a1,  a2 = (u(xm) - vm)/tau,
  *   x' = x + dt vm (wrapped once into [0, 2pi)),  v' = v + dt a2 rounded to f32,
  * with f64-accurate arithmetic (v is promoted from f32).  One pass over the planes per
- * step; each step is one kernel launch (capturable in a CUDA graph). */
+ * step; each step is one kernel launch (capturable in a CUDA graph).
+ * Defining passages: Eq. 1 (Sec. 2), the per-particle update of position from velocity
+ * that this step generalises to an inertial particle with a second-order integrator;
+ * Listing 4's commentary (Sec. 2) names temporary Runge-Kutta positions and velocities
+ * as typical particle data.  The paper gives no RK2 scheme: the midpoint rule, the ABC
+ * flow and tau are this library's workload definition, stated above. */
 int soax_step(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream);
 
 /* The same nsteps (>= 0) midpoint-RK2 steps as soax_step in ONE pass over the planes:
@@ -195,14 +200,19 @@ int soax_step(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream);
  * once at the end, wrapped into [0, 2pi).  Results therefore agree with soax_step to
  * within a few binary64 ulps per step, not bit for bit.  Positions on entry must lie in
  * [0, 8) (soax_step's output always does).  Tau and acceleration fields as for
- * soax_step; acc receives the last step's a2. */
+ * soax_step; acc receives the last step's a2.
+ * Defining passages: Eq. 1 (Sec. 2) as for soax_step; the single pass over all arrays is
+ * the loop fusion of the expression templates (Sec. 4.2, 4.2.2), applied across time
+ * steps. */
 int soax_step_fused(soax_t h, const soax_flow* fl, int32_t nsteps, void* stream);
 
 /* soax_step_fused that also writes the cell keys of the final positions (the flow's
  * position field) on a grid^3 grid into keys (n u32, 16-byte aligned, caller-owned),
  * bit-identical to soax_cell_keys on the result, as the particles are stored: the sort
  * that follows (soax_sort_by_keys) needs no key pass over the positions.  grid in
- * 1..1024.  nsteps = 0 writes the keys of the current positions. */
+ * 1..1024.  nsteps = 0 writes the keys of the current positions.
+ * Defining passages: Eq. 1 (Sec. 2) for the steps; the keys serve spatial locality of
+ * memory access (Sec. 1; the cache analysis of Sec. 2). */
 int soax_step_fused_keys(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t grid, uint32_t* keys,
                          void* stream);
 
@@ -214,19 +224,25 @@ int soax_step_fused_keys(soax_t h, const soax_flow* fl, int32_t nsteps, int32_t 
  * SOAX_EINVAL is recorded for soax_sync), e.g. the permutation soax_sort_perm left in a
  * sort workspace, so that a cell sort's gather costs no pass of its own.  grid = 0: no
  * keys (keys ignored); else keys as for soax_step_fused_keys.  Both buffer sets must be
- * bound. */
+ * bound.
+ * Defining passages: apply-to-all-arrays (Listing 7, Sec. 4.2.1) for the gather of every
+ * field; Eq. 1 (Sec. 2) for the steps; spatial locality (Sec. 1) for the cell order. */
 int soax_permute_step_fused(soax_t h, const uint32_t* perm, const soax_flow* fl, int32_t nsteps, int32_t grid,
                             uint32_t* keys, void* stream);
 
 /* The same step, bit-identical per particle, on AoS records in place (layout from
- * soax_aos_layout; the flow's field indices refer to this handle's schema). */
+ * soax_aos_layout; the flow's field indices refer to this handle's schema).
+ * Defining passages: the AoS records of Listings 1 and 4 and the AoS-versus-SoA
+ * comparison of Sec. 2 and Sec. 3.2, with soax_step's arithmetic. */
 int soax_step_aos(soax_t h, void* aos_dev, const soax_flow* fl, int32_t nsteps, void* stream);
 
 /* ------------------------------------------------------------- cell sort */
 
 /* keys[i] = (iz*G + iy)*G + ix of the live position field pos_field, with
  * i_d = min((int)(x_d * (G/2pi)), G-1) computed in binary64 (G/2pi rounded once).
- * grid G in 1..1024; keys: n u32, 16-byte aligned. */
+ * grid G in 1..1024; keys: n u32, 16-byte aligned.
+ * Defining passages: spatial locality of memory access (Sec. 1) and the cache analysis
+ * of Sec. 2; the paper defines no cell grid, which is this library's definition above. */
 int soax_cell_keys(soax_t h, int32_t pos_field, int32_t grid, uint32_t* keys, void* stream);
 
 /* Workspace bytes soax_radix_sort_pairs needs for n keys of key_bits significant bits. */
@@ -236,7 +252,11 @@ int soax_radix_workspace_bytes(int64_t n, int32_t key_bits, size_t* bytes);
  * of key.  vals_in may be NULL (then value i = i, i.e. vals_out is the stable argsort).
  * keys_out may be NULL (sorted keys not wanted).  Inputs are not modified; outputs must
  * not alias inputs.  All arrays hold n u32 and are 16-byte aligned; ws holds
- * soax_radix_workspace_bytes bytes. */
+ * soax_radix_workspace_bytes bytes.
+ * Defining passages: none in the paper (it has no sort); the ordering step behind the
+ * spatial locality of Sec. 1.  A scatter destination outside the output (only possible
+ * if the workspace is overwritten while the sort runs) is clamped to the last element
+ * and SOAX_EINVAL is recorded for soax_sync. */
 int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                           uint32_t* vals_out, int64_t n, int32_t key_bits, void* ws,
                           size_t ws_bytes, void* stream);
@@ -253,7 +273,9 @@ int soax_sort_workspace_bytes(soax_t h, int32_t grid, size_t* bytes);
 
 /* Cell keys of the field tagged 'P' on a grid^3 grid, stable radix sort, permute-gather
  * of all fields into the shadow set, flip.  The sorted keys and the permutation are left
- * in the workspace (soax_sort_results gives their addresses). */
+ * in the workspace (soax_sort_results gives their addresses).
+ * Defining passages: spatial locality (Sec. 1, Sec. 2's cache analysis) for the order;
+ * apply-to-all-arrays (Listing 7, Sec. 4.2.1) for the gather of every field. */
 int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_bytes, void* stream);
 int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_t** sorted_keys,
                       uint32_t** perm);
@@ -263,12 +285,13 @@ int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_bytes, uint32_
  * low bits up to grid^3 - 1 are sorted), permute-gather of all fields into the shadow
  * set, flip.  ws as for soax_sort_by_cell (soax_sort_results gives the sorted keys and
  * the permutation in it); keys must not overlap ws's sorted-key, permutation or radix
- * regions. */
+ * regions.  Defining passages: as for soax_sort_by_cell. */
 int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes, void* stream);
 
 /* soax_sort_by_keys without the permute-gather: the stable permutation that sorts keys
  * is left in ws (soax_sort_results gives its address; the sorted keys are not written);
- * no particle moves.  Pair it with soax_permute_step_fused, or soax_permute. */
+ * no particle moves.  Pair it with soax_permute_step_fused, or soax_permute.
+ * Defining passages: as for soax_sort_by_cell (the order only). */
 int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes, void* stream);
 
 /* soax_sort_by_cell without a caller workspace.  The paper has no counterpart: this is
@@ -280,8 +303,10 @@ int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_
  * library holds until exit; this call allocates nothing.  Limits: n <= 1048576 and
  * grid in 1..64 (SOAX_EINVAL otherwise, before any device work).  perm_out: n u32 on
  * the device receiving the permutation, or NULL.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the one array and it keeps the
+ * the array's device address (cudaGetSymbolAddress) with that device current, and a call
+ * looks it up again if the device's context has changed since (after cudaDeviceReset the
+ * array may sit elsewhere); make the first call, and the first after a reset, before any
+ * stream capture.  All calls share the one array and it keeps the
  * last call's contents (every part is rewritten before use): calls that overlap on the
  * GPU, on any stream or thread, race and corrupt each other. */
 int soax_sort_by_cell_noalloc(soax_t h, int32_t grid, uint32_t* perm_out, void* stream);
@@ -321,7 +346,12 @@ int soax_euler_aos(void* rec, int64_t n, int64_t record_bytes, int64_t x_off, in
 
 /* ---------------------------------------------------------------- adjoint */
 
-/* Workspace bytes for K steps with a checkpoint every ckpt_every steps. */
+/* Defining passages for the adjoint calls: the paper has no derivative of the step; they
+ * differentiate soax_step's operation (Eq. 1 generalised, Sec. 2) in reverse mode, the
+ * training-system form this library adds on top of it, with the loss of
+ * soax_minimage_loss.
+ *
+ * Workspace bytes for K steps with a checkpoint every ckpt_every steps. */
 int soax_adjoint_workspace_bytes(soax_t h, int32_t K, int32_t ckpt_every, size_t* bytes);
 
 /* Forward: K steps in place with soax_step_fused's arithmetic (bit-identical to
@@ -350,7 +380,12 @@ int soax_minimage_loss(soax_t h, int32_t pos_field, const double* const* xtgt, d
 
 /* ---------------------------------------------------------------- batched */
 
-/* Workspace bytes for advancing nens ensembles with soax_step_batched (any tune). */
+/* Defining passages for the batched calls: the paper runs one particle set per program
+ * (Sec. 2, 3); many independent sets advanced in one launch are this library's addition,
+ * with soax_step's arithmetic per particle (Eq. 1 generalised) and the particle-level data
+ * parallelism of the GPU SIMT model (Sec. 3.2).
+ *
+ * Workspace bytes for advancing nens ensembles with soax_step_batched (any tune). */
 int soax_batched_workspace_bytes(const soax_t* hs, int32_t nens, const soax_tune* tune,
                                  size_t* bytes);
 

@@ -69,7 +69,10 @@ extern "C" {
  * (workspace too small), SOAX_EALIGN, SOAX_EUNBOUND; all before any copy or launch.
  * SOAX_ECUDA if an event, copy or launch cannot be made (work enqueued before it
  * stays enqueued; a deferred call's downloads are then dropped).  Validation also
- * rejects defer other than 0 or 1. */
+ * rejects defer other than 0 or 1.
+ * Defining passages: host-device transfers and keeping the data on the device (Sec.
+ * 4.2.2); Eq. 1 (Sec. 2) for the steps; spatial locality (Sec. 1) for the cell order;
+ * apply-to-all-arrays (Listing 7) for the gather. */
 int soax_step_host(soax_t h, void* const* host, const soax_flow* fl, int32_t nsteps, int32_t grid, int32_t nchunks,
                    int32_t defer, void* ws, size_t ws_bytes, void* stream, void* up_stream, void* down_stream);
 

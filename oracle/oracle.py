@@ -42,7 +42,7 @@ def lib():
         L.orc_step_soa.argtypes = [i64, p, p, p, p, p, p, p, p, p, p, d, d, d, d, d, d, C.c_int, C.c_int]
         L.orc_step_aos.argtypes = [i64, p, i64, i64, i64, i64, i64, d, d, d, d, d, d, C.c_int, C.c_int]
         L.orc_step_one_detail.argtypes = [d, d, d, d, d, p, p, p, p]
-        L.orc_step_f64state.argtypes = [i64, p, p, p, p, p, p, d, d, d, d, d, C.c_int]
+        L.orc_step_f64state.argtypes = [i64, p, p, p, p, p, p, d, d, d, d, d, C.c_int, C.c_int]
         L.orc_cell_keys.argtypes = [i64, p, p, p, C.c_int, p]
         L.orc_stable_argsort.argtypes = [i64, p, p, p]
         L.orc_stable_argsort.restype = C.c_int
@@ -118,11 +118,11 @@ def step_one_detail(A, B, C_, tau, dt, x3, v3):
     return x, vn, a2
 
 
-def step_f64state(pos, vel, A, B, C_, tau, dt, nsteps):
+def step_f64state(pos, vel, A, B, C_, tau, dt, nsteps, threads=None):
     px, py, pz = (_need(a, np.float64) for a in pos)
     vx, vy, vz = (_need(a, np.float64) for a in vel)
     lib().orc_step_f64state(px.size, _p(px), _p(py), _p(pz), _p(vx), _p(vy), _p(vz), A, B, C_,
-                            tau, dt, int(nsteps))
+                            tau, dt, int(nsteps), threads or default_threads())
 
 
 def cell_keys(px, py, pz, G):

@@ -198,20 +198,32 @@ void orc_step_one_detail(double A, double B, double C, double tau, double dt, do
 
 /* FP64-state forward (velocity never rounded to f32): used for finite differences
  * and the FP64 adjoint. */
-void orc_step_f64state(int64_t n, double* px, double* py, double* pz, double* vx, double* vy,
-                       double* vz, double A, double B, double C, double tau, double dt,
-                       int nsteps) {
-  double inv_tau = 1.0 / tau;
-  for (int64_t i = 0; i < n; ++i) {
-    double x[3] = {px[i], py[i], pz[i]}, v[3] = {vx[i], vy[i], vz[i]};
-    for (int s = 0; s < nsteps; ++s) {
+typedef struct {
+  double *px, *py, *pz, *vx, *vy, *vz;
+  double A, B, C, tau, dt;
+  int nsteps;
+} f64state_ctx;
+
+static void f64state_range(void* p, int64_t lo, int64_t hi) {
+  f64state_ctx* c = (f64state_ctx*)p;
+  double inv_tau = 1.0 / c->tau;
+  for (int64_t i = lo; i < hi; ++i) {
+    double x[3] = {c->px[i], c->py[i], c->pz[i]}, v[3] = {c->vx[i], c->vy[i], c->vz[i]};
+    for (int s = 0; s < c->nsteps; ++s) {
       double vn[3], a2[3];
-      rk2_core(A, B, C, inv_tau, dt, x, v, vn, a2);
+      rk2_core(c->A, c->B, c->C, inv_tau, c->dt, x, v, vn, a2);
       v[0] = vn[0]; v[1] = vn[1]; v[2] = vn[2];
     }
-    px[i] = x[0]; py[i] = x[1]; pz[i] = x[2];
-    vx[i] = v[0]; vy[i] = v[1]; vz[i] = v[2];
+    c->px[i] = x[0]; c->py[i] = x[1]; c->pz[i] = x[2];
+    c->vx[i] = v[0]; c->vy[i] = v[1]; c->vz[i] = v[2];
   }
+}
+
+void orc_step_f64state(int64_t n, double* px, double* py, double* pz, double* vx, double* vy,
+                       double* vz, double A, double B, double C, double tau, double dt,
+                       int nsteps, int nthreads) {
+  f64state_ctx c = {px, py, pz, vx, vy, vz, A, B, C, tau, dt, nsteps};
+  parallel_for(n, nthreads, f64state_range, &c);
 }
 
 /* ------------------------------------------------------------- cell keys */

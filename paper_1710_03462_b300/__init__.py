@@ -85,6 +85,22 @@ def _ptr3(ts):
     return (C.c_void_p * 3)(*[t.data_ptr() for t in ts])
 
 
+def _hold(stream, *tensors):
+    """Keep device memory this binding allocated for a call alive until the call's work
+    on `stream` has run.  The caching allocator frees a tensor against the stream that is
+    current when it was allocated; a call launched on another stream can still be using
+    it after this function returns, so the tensor is marked as used by that stream too."""
+    if stream is None:
+        return
+    if stream == torch.cuda.current_stream(stream.device):
+        return
+    for t in tensors:
+        if isinstance(t, (list, tuple)):
+            _hold(stream, *t)
+        elif t is not None and t.is_cuda:
+            t.record_stream(stream)
+
+
 def sync(stream=None):
     """Synchronise the stream and report a device-side error as SoaxError."""
     _check(lib().soax_sync(_stream(stream)), "soax_sync")
@@ -210,7 +226,8 @@ class Particles:
         down_stream (two streams of this object when not given).  defer: leave the
         downloads to the next step_host call (interleaved with its uploads) or to
         step_host_finish; the live planes must not change meanwhile.  Returns the
-        permutation (int32 view into ws)."""
+        permutation (int32 view into ws); with the workspace this object keeps (ws None),
+        the next step_host call overwrites it, so it is valid until then."""
         ptrs = []
         for name, dt, nc, _ in self.schema:
             comps = host[name]
@@ -227,10 +244,11 @@ class Particles:
             # live there until its device work has run, which can be long after the call
             # returns (a workspace freed on return could be handed to other work while the
             # call's sort still writes into it).
+            # Keyed by the grid and the current size: the workspace grows with n (set_size).
             cache = self.__dict__.setdefault("_host_ws", {})
-            if grid not in cache:
-                cache[grid] = self.sort_workspace(grid)
-            ws = cache[grid]
+            if (grid, self.n) not in cache:
+                cache[(grid, self.n)] = self.sort_workspace(grid)
+            ws = cache[(grid, self.n)]
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         if s != torch.cuda.current_stream(self.device):
             ws.record_stream(s)
@@ -279,6 +297,7 @@ class Particles:
         if perm is not None:
             if grid is not None and keys is None:
                 keys = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.device)
+                _hold(stream, keys)
             _check(lib().soax_permute_step_fused(self.h, _ptr(perm), C.byref(fl), int(nsteps),
                                                  int(grid) if grid is not None else 0, _ptr(keys), _stream(stream)),
                    "soax_permute_step_fused")
@@ -288,6 +307,7 @@ class Particles:
             return None
         if keys is None:
             keys = torch.empty(max(self.n, 1), dtype=torch.int32, device=self.device)
+            _hold(stream, keys)
         _check(lib().soax_step_fused_keys(self.h, C.byref(fl), int(nsteps), int(grid), _ptr(keys), _stream(stream)),
                "soax_step_fused_keys")
         return keys
@@ -303,7 +323,9 @@ class Particles:
         return torch.empty(self.n * rb, dtype=torch.uint8, device=self.device)
 
     def to_aos(self, out=None, stream=None):
-        out = self.new_aos() if out is None else out
+        if out is None:
+            out = self.new_aos()
+            _hold(stream, out)
         _check(lib().soax_soa_to_aos(self.h, _ptr(out), _stream(stream)), "soax_soa_to_aos")
         return out
 
@@ -315,7 +337,9 @@ class Particles:
         _check(lib().soax_step_aos(self.h, _ptr(aos), C.byref(fl), int(nsteps), _stream(stream)), "soax_step_aos")
 
     def cell_keys(self, grid, pos="pos", out=None, stream=None):
-        out = torch.empty(self.n, dtype=torch.int32, device=self.device) if out is None else out
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int32, device=self.device)
+            _hold(stream, out)
         _check(lib().soax_cell_keys(self.h, self.fidx(pos), int(grid), _ptr(out), _stream(stream)), "soax_cell_keys")
         return out
 
@@ -326,14 +350,18 @@ class Particles:
 
     def sort_by_cell(self, grid, ws=None, stream=None):
         """Cell sort of every field; returns (sorted keys, perm) as int32 views into ws."""
-        ws = self.sort_workspace(grid) if ws is None else ws
+        if ws is None:
+            ws = self.sort_workspace(grid)
+            _hold(stream, ws)
         _check(lib().soax_sort_by_cell(self.h, int(grid), _ptr(ws), ws.numel(), _stream(stream)), "soax_sort_by_cell")
         return self.sort_results(grid, ws)
 
     def sort_by_keys(self, grid, keys, ws=None, stream=None):
         """sort_by_cell with the keys given (from step_fused(..., keys=...) or cell_keys):
         no key pass.  Returns (sorted keys, perm) as int32 views into ws."""
-        ws = self.sort_workspace(grid) if ws is None else ws
+        if ws is None:
+            ws = self.sort_workspace(grid)
+            _hold(stream, ws)
         _check(lib().soax_sort_by_keys(self.h, int(grid), _ptr(keys), _ptr(ws), ws.numel(), _stream(stream)),
                "soax_sort_by_keys")
         return self.sort_results(grid, ws)
@@ -341,7 +369,9 @@ class Particles:
     def sort_perm(self, grid, keys, ws=None, stream=None):
         """The stable permutation sorting keys, left in ws (no particle moves); returns
         (None, perm) with perm an int32 view into ws (the sorted keys are not written)."""
-        ws = self.sort_workspace(grid) if ws is None else ws
+        if ws is None:
+            ws = self.sort_workspace(grid)
+            _hold(stream, ws)
         _check(lib().soax_sort_perm(self.h, int(grid), _ptr(keys), _ptr(ws), ws.numel(), _stream(stream)),
                "soax_sort_perm")
         return None, self.sort_results(grid, ws)[1]
@@ -373,6 +403,7 @@ class Particles:
         """Particle i as one AoS record (uint8 tensor of the record size, Listing 6)."""
         rb, _ = self.aos_layout()
         rec = torch.empty(max(rb, 16), dtype=torch.uint8, device=self.device)
+        _hold(stream, rec)
         _check(lib().soax_get_element(self.h, int(i), _ptr(rec), _stream(stream)), "soax_get_element")
         return rec[:rb]
 
@@ -392,6 +423,7 @@ class Particles:
         b = C.c_size_t()
         _check(lib().soax_remove_workspace_bytes(k, C.byref(b)))
         ws = torch.empty(max(b.value, 16), dtype=torch.uint8, device=self.device)
+        _hold(stream, ws)
         _check(lib().soax_remove(self.h, _ptr(idx), k, _ptr(ws), ws.numel(), _stream(stream)), "soax_remove")
         self.n -= k
 
@@ -436,6 +468,7 @@ class Particles:
         grad = torch.empty(4, dtype=torch.float64, device=self.device)
         xk = [t.contiguous() for t in xbarK]
         vk = [t.contiguous() for t in vbarK] if vbarK is not None else None
+        _hold(stream, xb0, vb0, grad, xk, vk)
         _check(lib().soax_step_adjoint(self.h, C.byref(fl), int(K), int(ckpt_every), _ptr(ws), ws.numel(),
                                        _ptr3(xk), _ptr3(vk), _ptr3(xb0), _ptr3(vb0), _ptr(grad), _stream(stream)),
                "soax_step_adjoint")
@@ -445,6 +478,7 @@ class Particles:
         loss = torch.empty(1, dtype=torch.float64, device=self.device)
         xb = [torch.empty(self.n, dtype=torch.float64, device=self.device) for _ in range(3)] if want_grad else None
         xt = [t.contiguous() for t in xtgt]
+        _hold(stream, loss, xb, xt)
         _check(lib().soax_minimage_loss(self.h, self.fidx(pos), _ptr3(xt), _ptr(loss), _ptr3(xb), _ptr(ws),
                                         ws.numel(), _stream(stream)), "soax_minimage_loss")
         return loss, xb
@@ -456,9 +490,12 @@ def radix_sort_pairs(keys, vals=None, key_bits=32, want_keys=True, ws=None, stre
     n = keys.numel()
     b = C.c_size_t()
     _check(lib().soax_radix_workspace_bytes(n, int(key_bits), C.byref(b)))
-    ws = torch.empty(max(b.value, 16), dtype=torch.uint8, device=keys.device) if ws is None else ws
+    if ws is None:
+        ws = torch.empty(max(b.value, 16), dtype=torch.uint8, device=keys.device)
+        _hold(stream, ws)
     ko = torch.empty_like(keys) if want_keys else None
     vo = torch.empty(n, dtype=torch.int32, device=keys.device)
+    _hold(stream, ko, vo)
     _check(lib().soax_radix_sort_pairs(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), n, int(key_bits), _ptr(ws),
                                        ws.numel(), _stream(stream)), "soax_radix_sort_pairs")
     return ko, vo
@@ -497,7 +534,9 @@ def step_batched(parts, flows, nsteps, tune: Tune = None, ws=None, stream=None):
     (bit-identical to Particles.step_fused per ensemble).  The first call for a new
     (ensembles, tune, ws) uploads a tile plan and synchronises; later identical calls only
     launch."""
-    ws = batched_workspace(parts) if ws is None else ws
+    if ws is None:
+        ws = batched_workspace(parts)
+        _hold(stream, ws)
     t = tune.c() if tune is not None else None
     _check(lib().soax_step_batched(_handles(parts), _flows(parts, flows), len(parts), int(nsteps),
                                    C.byref(t) if t is not None else None, _ptr(ws), ws.numel(), _stream(stream)),

@@ -42,18 +42,57 @@ int dtype_size(int dtype) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-int* status_word() {
-  static std::mutex mu;
-  static int* ptr[64] = {};
+unsigned long long current_context_id() {
+  // cuCtxGetCurrent and cuCtxGetId through the runtime's driver entry points (no link
+  // against libcuda).  A context's id is unique for the life of the process, so a device
+  // whose primary context was destroyed and created again (cudaDeviceReset) gets a new id.
+  typedef int (*get_current_t)(void**);
+  typedef int (*get_id_t)(void*, unsigned long long*);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<get_current_t>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<get_id_t>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return 0;
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+int device_symbol_address(const void* symbol, SymbolCache* cache, void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!ptr[dev]) {
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= SymbolCache::kDevices) return fail(SOAX_EUNSUPPORTED, "device index >= 64");
+  std::lock_guard<std::mutex> lk(cache->mu);
+  unsigned long long id = current_context_id();
+  if (id == 0 || cache->ctx[dev] != id || !cache->ptr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
-    ptr[dev] = static_cast<int*>(p);
+    e = cudaGetSymbolAddress(&p, symbol);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress");
+    cache->ptr[dev] = p;
+    cache->ctx[dev] = current_context_id();  // the lookup makes the primary context current
   }
-  return ptr[dev];
+  *out = cache->ptr[dev];
+  return SOAX_OK;
+}
+
+int* status_word() {
+  static SymbolCache cache;
+  void* p = nullptr;
+  if (device_symbol_address(&g_status_word, &cache, &p) != SOAX_OK) return nullptr;
+  return static_cast<int*>(p);
 }
 
 int check_handle(soax_t h) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -47,7 +48,22 @@ int cuda_fail(cudaError_t e, const char* what);
 int check_launch(const char* what);
 
 int dtype_size(int dtype);
-// Device address of this device's status word (looked up once per device), or null.
+// Id of the calling thread's current CUDA context (0 if none or unknown).
+unsigned long long current_context_id();
+// Per-device cache of a __device__ variable's address, valid for one context.
+struct SymbolCache {
+  static constexpr int kDevices = 64;
+  std::mutex mu;
+  void* ptr[kDevices] = {};
+  unsigned long long ctx[kDevices] = {};
+};
+// Device address of a __device__ variable on the current device: looked up with
+// cudaGetSymbolAddress on the first call for that device and again whenever the current
+// context is not the one the cached address was taken in (after cudaDeviceReset the
+// module is loaded again and the variable may move).  The lookup can load the module, so
+// the first call on a device belongs before any stream capture.
+int device_symbol_address(const void* symbol, SymbolCache* cache, void** out);
+// Device address of this device's status word, or null.
 int* status_word();
 bool aligned16(const void* p);
 

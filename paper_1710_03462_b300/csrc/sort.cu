@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scan_rows(uint32_t* __re
 __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n, int shift, uint32_t mask, int64_t nblocks,
-    const uint32_t* __restrict__ counts) {
+    const uint32_t* __restrict__ counts, int* __restrict__ status) {
   extern __shared__ uint32_t sm[];
   const int radix = (int)mask + 1;
   uint32_t* wc = sm;                         // [warps][radix]: per-warp digit counts, then prefixes
@@ -256,14 +256,19 @@ __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
     }
   }
   __syncthreads();
+  bool over = false;
   for (int li = tid; li < tcount; li += kSortBlock) {
     uint32_t key = sk[li];
     // Only a corrupted workspace (digit offsets overwritten meanwhile) puts dest outside
-    // the output: it is clamped to the last element rather than written out of bounds.
-    const uint32_t dest = min(gbase[(key >> shift) & mask] + (uint32_t)li, (uint32_t)n - 1u);  // n < 2^31
+    // the output: it is clamped to the last element rather than written out of bounds,
+    // and recorded once per thread after the loop.
+    const uint32_t raw = gbase[(key >> shift) & mask] + (uint32_t)li;
+    over |= raw >= (uint32_t)n;  // n < 2^31
+    const uint32_t dest = min(raw, (uint32_t)n - 1u);
     if (keys_out) keys_out[dest] = key;
     vals_out[dest] = sv[li];
   }
+  if (over) atomicExch(status, (int)SOAX_EINVAL);
 }
 
 static size_t downsweep_smem(int radix) { return (size_t)(kSortWarps * radix + 2 * radix + 2 * kTile) * 4; }
@@ -424,6 +429,8 @@ extern "C" int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* va
   uint32_t* ak[2] = {reinterpret_cast<uint32_t*>(w + p.off_ak[0]), reinterpret_cast<uint32_t*>(w + p.off_ak[1])};
   uint32_t* av[2] = {reinterpret_cast<uint32_t*>(w + p.off_av[0]), reinterpret_cast<uint32_t*>(w + p.off_av[1])};
   cudaStream_t s = as_stream(stream);
+  int* status = status_word();
+  if (!status) return fail(SOAX_ECUDA, "soax_radix_sort_pairs: status word");
   for (int pass = 0; pass < p.passes; ++pass) {
     const int shift = pass * p.width;
     const int width = key_bits - shift < p.width ? key_bits - shift : p.width;
@@ -441,7 +448,7 @@ extern "C" int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* va
     k_radix_scan_rows<<<radix, kScanThreads, 0, s>>>(counts, totals, p.nblocks);
     if (int r = check_launch("radix scan")) return r;
     k_radix_downsweep<<<(unsigned)p.nblocks, kSortBlock, downsweep_smem(radix), s>>>(kin, vin, kout, vout, n, shift,
-                                                                                    mask, p.nblocks, counts);
+                                                                                    mask, p.nblocks, counts, status);
     if (int r = check_launch("radix downsweep")) return r;
   }
   return SOAX_OK;

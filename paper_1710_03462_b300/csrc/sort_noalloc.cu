@@ -11,8 +11,6 @@
 // workspace.  The array is sized for at most kNoAllocMaxParticles particles on a grid of
 // at most kNoAllocMaxGrid cells per side; every GPU that loads the library holds it
 // until the process exits.
-#include <mutex>
-
 #include "soax_internal.h"
 
 namespace {
@@ -23,24 +21,15 @@ constexpr size_t kNoAllocScratchBytes = size_t(22) << 20;   // 22 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch per device, looked up once with that device current.
-// (In host code the array's name is only a host-side stand-in, never a device address.)
-std::mutex g_noalloc_mu;
-void* g_noalloc_dev_ptr[64] = {};
+// Device address of g_noalloc_scratch per device and context: looked up with that device
+// current on its first use, and again if the context changed since (cudaDeviceReset
+// reloads the module).  In host code the array's name is only a host-side stand-in, never
+// a device address.
+soax::SymbolCache g_noalloc_cache;
 
 int noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return soax::cuda_fail(e, "soax_sort_by_cell_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= 64) return soax::fail(SOAX_EUNSUPPORTED, "soax_sort_by_cell_noalloc: device index >= 64");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_dev_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return soax::cuda_fail(e, "soax_sort_by_cell_noalloc: cudaGetSymbolAddress");
-    g_noalloc_dev_ptr[dev] = p;
-  }
-  *out = g_noalloc_dev_ptr[dev];
+  if (int r = soax::device_symbol_address(&g_noalloc_scratch, &g_noalloc_cache, out))
+    return soax::fail(r, std::string("soax_sort_by_cell_noalloc: ") + soax_last_error());
   return SOAX_OK;
 }
 

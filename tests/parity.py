@@ -33,6 +33,31 @@ def out_of_tolerance(gpos, gvel, opos, ovel):
     return bad
 
 
+def assert_acc(gacc, oacc, gpos, gvel, opos, ovel):
+    """The stored acceleration is f32(a2) of the last step: one rounding of a
+    binary64-accurate value.  On particles whose stored velocities equal the oracle's bit
+    for bit and whose positions agree within 1e-12, it must equal the oracle's f32 value
+    or be one f32 ulp away (a2 within the step's error of a rounding midpoint).  A particle
+    that took an accepted velocity flip (audited through its position and velocity) follows
+    the flipped trajectory: a one-ulp change of v moves a2 by about ulp(v)/tau, so there
+    acc is held to the velocity tolerance, 1e-5 relative with a 1e-6 absolute floor."""
+    same = np.ones(gacc[0].size, bool)
+    for c in range(3):
+        d = np.abs(gpos[c] - opos[c])
+        same &= np.minimum(d, sx.TWO_PI - d) <= 1e-12
+        same &= gvel[c] == ovel[c]
+    for c in range(3):
+        g = np.ascontiguousarray(gacc[c], np.float32)
+        o = np.ascontiguousarray(oacc[c], np.float32)
+        up = np.nextafter(o, np.float32(np.inf))
+        dn = np.nextafter(o, np.float32(-np.inf))
+        ulp_ok = (g == o) | (g == up) | (g == dn)
+        assert np.all(ulp_ok[same]), f"acc[{c}]: {np.count_nonzero(~ulp_ok[same])} particles beyond one f32 ulp"
+        near = np.abs(g.astype(np.float64) - o) <= 1e-5 * np.abs(o) + 1e-6
+        assert np.all(near[~same]), f"acc[{c}]: a flipped particle beyond the velocity tolerance"
+    return int(np.count_nonzero(same))
+
+
 def gpu_one_step(x3, v3, A, B, C, tau, dt):
     p = sx.Particles([("pos", "f64", 3, "P"), ("vel", "f32", 3, "V")], 1, shadow=False)
     p.load({"pos": [np.array([x]) for x in x3], "vel": [np.array([v], np.float32) for v in v3]})

@@ -307,3 +307,16 @@ def test_speed_bound_per_step():
     oracle.step_soa(pos, vel, A, 0.0, 0.0, tau, dt, 1)
     vx = float(vel[0][0])
     assert M * (1.0 + h * h) * (1.0 - 1e-6) < vx <= M * (1.0 + h * h) * (1.0 + 2.0 ** -23)
+
+
+def test_f64state_threads_do_not_change_bits():
+    """Threads only split the particle range: one thread and many give the same bits."""
+    d = soax_inputs.basic_set(5000, 11)
+    outs = []
+    for threads in (1, 7):
+        p = [a.copy() for a in d["pos"]]
+        v = [a.astype(np.float64) for a in d["vel"]]
+        oracle.step_f64state(p, v, 1.0, 0.9, 1.1, 0.1, 1e-3, 20, threads=threads)
+        outs.append(p + v)
+    for a, b in zip(*outs):
+        assert a.tobytes() == b.tobytes()
