@@ -328,6 +328,46 @@ int soax_fill(soax_t h, int32_t field, double value, void* stream);
 int soax_lincomb(soax_t h, int32_t dst_field, int32_t dst_comp, int32_t nterms, const int32_t* src_fields,
                  const int32_t* src_comps, const double* coefs, double constant, void* stream);
 
+/* One operation of a whole-array expression (soax_expr): a postfix program evaluated
+ * element by element on a stack of values of the compute type. */
+typedef enum {
+  SOAX_EXPR_LOAD = 0,  /* push element i of plane (field, comp) of the live set, converted
+                          to the compute type as a C cast would (rounded to nearest)     */
+  SOAX_EXPR_CONST = 1, /* push value, rounded to the compute type                        */
+  SOAX_EXPR_ADD = 2,   /* pop b, pop a, push a + b (one IEEE rounding; SUB, MUL, DIV alike) */
+  SOAX_EXPR_SUB = 3,
+  SOAX_EXPR_MUL = 4,
+  SOAX_EXPR_DIV = 5,
+  SOAX_EXPR_NEG = 6,   /* pop a, push -a                                                 */
+  SOAX_EXPR_ABS = 7,   /* pop a, push |a|                                                */
+  SOAX_EXPR_SQRT = 8,  /* pop a, push sqrt(a), correctly rounded                         */
+  SOAX_EXPR_MIN = 9,   /* pop b, pop a, push (a < b ? a : b)                             */
+  SOAX_EXPR_MAX = 10,  /* pop b, pop a, push (a > b ? a : b)                             */
+  SOAX_EXPR_FMA = 11   /* pop c, pop b, pop a, push a*b + c with one rounding            */
+} soax_expr_opcode;
+
+typedef struct {
+  int32_t op;     /* soax_expr_opcode                          */
+  int32_t field;  /* SOAX_EXPR_LOAD: field index; else ignored  */
+  int32_t comp;   /* SOAX_EXPR_LOAD: component; else ignored    */
+  int32_t pad;
+  double value;   /* SOAX_EXPR_CONST: the constant; else ignored */
+} soax_expr_op;
+
+/* General whole-array expression, one pass over the planes it reads and writes (the
+ * expression templates of Sec. 4.2 -- posArr(0) = velArr(1) - velArr(2) in Listing 5 --
+ * with the loop fusion of Sec. 4.2.2, as a program chosen at run time): for every
+ * particle i, run the postfix program prog[0..nops-1] with element i of each loaded plane
+ * and store the one value left into plane (dst_field, dst_comp), rounded to its type.
+ * Sources may have any type (mixed-type expressions); the arithmetic runs in
+ * compute_dtype (SOAX_F32 or SOAX_F64), every operation rounded as IEEE 754 specifies
+ * (no contraction: a*b + c is two roundings unless written as SOAX_EXPR_FMA).  The
+ * destination must be an f32 or f64 field and may also be a source.  Limits: nops in
+ * 1..64, at most 16 loads, stack depth at most 16; the program must never pop an empty
+ * stack and must leave exactly one value (SOAX_EINVAL otherwise, before any launch). */
+int soax_expr(soax_t h, int32_t dst_field, int32_t dst_comp, const soax_expr_op* prog, int32_t nops,
+              int32_t compute_dtype, void* stream);
+
 /* ------------------------------------------------- Euler step (Eq. 1) */
 
 /* The paper's benchmark step x += dt*v (Eq. 1, Sec. 2) in single precision on the live

@@ -19,6 +19,7 @@ in soax_oracle.c.  Functions:
   fill(plane, value)                        SetToValue on one array (Listing 7)
   lincomb(dst, srcs, coefs, constant)       dst = constant + sum coef_k src_k (Listing 5)
   remove(planes, idx)                       removal by overwriting with the last ones (Sec. 2)
+  expr(program, compute, out_dtype)         a postfix expression over whole arrays (Sec. 4.2)
 """
 import ctypes as C
 import os
@@ -60,6 +61,7 @@ def lib():
         L.orc_remove.argtypes = [i64, C.c_int, p, p, p, i64]
         L.orc_remove.restype = i64
         L.orc_lincomb.argtypes = [i64, C.c_int, p, C.c_int, p, p, d]
+        L.orc_expr.argtypes = [i64, C.c_int, C.c_int, p, p, p, p, p, C.c_int]
         _lib = L
     return _lib
 
@@ -258,3 +260,40 @@ def remove(planes, idx):
     eb = np.array([a.dtype.itemsize for a in planes], np.int32)
     m = lib().orc_remove(n, k, arr, _p(eb), _p(idx), idx.size)
     return [a[:m].copy() for a in planes]
+
+
+_EXPR_OPS = {"load": 0, "const": 1, "add": 2, "sub": 3, "mul": 4, "div": 5, "neg": 6, "abs": 7, "sqrt": 8,
+             "min": 9, "max": 10, "fma": 11}
+
+
+def expr(program, compute="f64", out_dtype=np.float64):
+    """Evaluate a postfix program element by element (orc_expr).  program: a list of
+    ("load", array), ("const", value) or an operator name (add, sub, mul, div, neg, abs,
+    sqrt, min, max, fma); compute: "f32" or "f64"; every loaded array has the same length.
+    Returns the result array of out_dtype (float32 or float64)."""
+    ops, vals, srcs, codes, keep = [], [], [], [], []
+    n = None
+    for item in program:
+        name, arg = (item, None) if isinstance(item, str) else item
+        ops.append(_EXPR_OPS[name])
+        vals.append(float(arg) if name == "const" else 0.0)
+        if name == "load":
+            a = np.ascontiguousarray(arg)
+            n = a.size if n is None else n
+            if a.size != n:
+                raise ValueError("expr: loaded arrays differ in length")
+            keep.append(a)
+            srcs.append(a.ctypes.data)
+            codes.append(_TCODES[a.dtype])
+        else:
+            srcs.append(None)
+            codes.append(0)
+    n = 0 if n is None else n
+    out = np.empty(n, out_dtype)
+    op = np.array(ops, np.int32)
+    val = np.array(vals, np.float64)
+    code = np.array(codes, np.int32)
+    arr = (C.c_void_p * len(srcs))(*srcs)
+    lib().orc_expr(n, 1 if compute == "f32" else 0, len(ops), _p(op), _p(val), arr, _p(code), _p(out),
+                   1 if np.dtype(out_dtype) == np.float32 else 0)
+    return out

@@ -546,3 +546,91 @@ int64_t orc_remove(int64_t n, int nplanes, void* const* planes, const int32_t* e
   free(removed);
   return m;
 }
+
+/* ------------------------------------------------- general expressions (Sec. 4.2) */
+/* An expression over whole arrays (the expression templates of Sec. 4.2, e.g. Listing
+ * 5's posArr(0) = velArr(1) - velArr(2)), written as a postfix program evaluated element
+ * by element on a stack of values of the compute type (binary32 when is_f32, else
+ * binary64).  Operation codes (op[j]):
+ *   0 LOAD  push source j converted to the compute type (as a C cast: exact for every
+ *           source type in binary64 except i64 beyond 2^53; rounded to nearest in
+ *           binary32 for i32, i64 and f64 sources)
+ *   1 CONST push value[j] rounded to the compute type
+ *   2 ADD, 3 SUB, 4 MUL, 5 DIV: pop b, pop a, push a op b, correctly rounded
+ *   6 NEG, 7 ABS, 8 SQRT (correctly rounded): pop a, push f(a)
+ *   9 MIN, 10 MAX: pop b, pop a, push (a < b ? a : b), (a > b ? a : b)
+ *  11 FMA: pop c, pop b, pop a, push a*b+c with one rounding
+ * The result (the one value left) is stored into dst, rounded to the destination type
+ * (dst_is_f32) when that is narrower.  src_tcode[j] is the type code of source j (0 i32,
+ * 1 i64, 2 u8, 3 f32, 4 f64); src[j] is unused unless op[j] is LOAD.  The program is
+ * assumed valid (the library checks its own before any launch). */
+static double expr_load_d(const void* p, int t, int64_t i) {
+  switch (t) {
+    case 0: return (double)((const int32_t*)p)[i];
+    case 1: return (double)((const int64_t*)p)[i];
+    case 2: return (double)((const uint8_t*)p)[i];
+    case 3: return (double)((const float*)p)[i];
+    default: return ((const double*)p)[i];
+  }
+}
+
+static float expr_load_f(const void* p, int t, int64_t i) {
+  switch (t) {
+    case 0: return (float)((const int32_t*)p)[i];
+    case 1: return (float)((const int64_t*)p)[i];
+    case 2: return (float)((const uint8_t*)p)[i];
+    case 3: return ((const float*)p)[i];
+    default: return (float)((const double*)p)[i];
+  }
+}
+
+void orc_expr(int64_t n, int is_f32, int nops, const int32_t* op, const double* value, const void* const* src,
+              const int32_t* src_tcode, void* dst, int dst_is_f32) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (is_f32) {
+      float st[64];
+      int sp = 0;
+      for (int j = 0; j < nops; ++j) {
+        float a, b, c;
+        switch (op[j]) {
+          case 0: st[sp++] = expr_load_f(src[j], src_tcode[j], i); break;
+          case 1: st[sp++] = (float)value[j]; break;
+          case 2: b = st[--sp]; a = st[--sp]; st[sp++] = a + b; break;
+          case 3: b = st[--sp]; a = st[--sp]; st[sp++] = a - b; break;
+          case 4: b = st[--sp]; a = st[--sp]; st[sp++] = a * b; break;
+          case 5: b = st[--sp]; a = st[--sp]; st[sp++] = a / b; break;
+          case 6: a = st[--sp]; st[sp++] = -a; break;
+          case 7: a = st[--sp]; st[sp++] = fabsf(a); break;
+          case 8: a = st[--sp]; st[sp++] = sqrtf(a); break;
+          case 9: b = st[--sp]; a = st[--sp]; st[sp++] = a < b ? a : b; break;
+          case 10: b = st[--sp]; a = st[--sp]; st[sp++] = a > b ? a : b; break;
+          default: c = st[--sp]; b = st[--sp]; a = st[--sp]; st[sp++] = fmaf(a, b, c); break;
+        }
+      }
+      if (dst_is_f32) ((float*)dst)[i] = st[0];
+      else ((double*)dst)[i] = (double)st[0];
+    } else {
+      double st[64];
+      int sp = 0;
+      for (int j = 0; j < nops; ++j) {
+        double a, b, c;
+        switch (op[j]) {
+          case 0: st[sp++] = expr_load_d(src[j], src_tcode[j], i); break;
+          case 1: st[sp++] = value[j]; break;
+          case 2: b = st[--sp]; a = st[--sp]; st[sp++] = a + b; break;
+          case 3: b = st[--sp]; a = st[--sp]; st[sp++] = a - b; break;
+          case 4: b = st[--sp]; a = st[--sp]; st[sp++] = a * b; break;
+          case 5: b = st[--sp]; a = st[--sp]; st[sp++] = a / b; break;
+          case 6: a = st[--sp]; st[sp++] = -a; break;
+          case 7: a = st[--sp]; st[sp++] = fabs(a); break;
+          case 8: a = st[--sp]; st[sp++] = sqrt(a); break;
+          case 9: b = st[--sp]; a = st[--sp]; st[sp++] = a < b ? a : b; break;
+          case 10: b = st[--sp]; a = st[--sp]; st[sp++] = a > b ? a : b; break;
+          default: c = st[--sp]; b = st[--sp]; a = st[--sp]; st[sp++] = fma(a, b, c); break;
+        }
+      }
+      if (dst_is_f32) ((float*)dst)[i] = (float)st[0];
+      else ((double*)dst)[i] = st[0];
+    }
+  }
+}

@@ -17,6 +17,7 @@ device array per component.  On top of it the library runs
 
 There is no CPU fallback: if the library cannot be loaded, every call raises.
 """
+import ast
 import ctypes as C
 import hashlib
 import json
@@ -26,10 +27,11 @@ from dataclasses import dataclass
 import torch
 
 from . import _abi
-from ._abi import DTYPES, STATUS_NAMES, soax_field_desc, soax_flow, soax_tune
+from ._abi import DTYPES, EXPR_OPS, STATUS_NAMES, soax_expr_op, soax_field_desc, soax_flow, soax_tune
 
 __all__ = ["SoaxError", "lib", "Particles", "Flow", "Tune", "radix_sort_pairs", "step_batched", "euler_aos",
-           "batched_workspace", "autotune", "sync", "SoaxRK2", "TWO_PI", "BASIC_SCHEMA", "WIDE_SCHEMA"]
+           "batched_workspace", "autotune", "sync", "SoaxRK2", "TWO_PI", "BASIC_SCHEMA", "WIDE_SCHEMA",
+           "parse_expr"]
 
 TWO_PI = 6.283185307179586
 
@@ -42,6 +44,47 @@ WIDE_SCHEMA = [("id", "i64", 1, "N"), ("pos", "f64", 3, "P"), ("vel", "f32", 3, 
 
 TORCH_DTYPES = {"i32": torch.int32, "i64": torch.int64, "u8": torch.uint8, "f32": torch.float32,
                 "f64": torch.float64}
+
+
+_BINOPS = {ast.Add: "add", ast.Sub: "sub", ast.Mult: "mul", ast.Div: "div"}
+_CALLS = {"sqrt": ("sqrt", 1), "abs": ("abs", 1), "min": ("min", 2), "max": ("max", 2), "fma": ("fma", 3)}
+
+
+def parse_expr(text):
+    """An infix expression over fields -- "vel[1] * vel[2] / mass + 0.5", "sqrt(fma(a, b, c))"
+    -- as the postfix program soax_expr runs: a list of ("load", field, comp),
+    ("const", value) and operator names, in Python's operator precedence, left to right.
+    A field without a subscript is component 0.  Functions: sqrt, abs, min, max, fma."""
+    def walk(node, out):
+        if isinstance(node, ast.BinOp) and type(node.op) in _BINOPS:
+            walk(node.left, out)
+            walk(node.right, out)
+            out.append(_BINOPS[type(node.op)])
+        elif isinstance(node, ast.UnaryOp) and isinstance(node.op, (ast.USub, ast.UAdd)):
+            walk(node.operand, out)
+            if isinstance(node.op, ast.USub):
+                out.append("neg")
+        elif isinstance(node, ast.Call) and isinstance(node.func, ast.Name) and node.func.id in _CALLS:
+            name, arity = _CALLS[node.func.id]
+            if len(node.args) != arity or node.keywords:
+                raise ValueError(f"parse_expr: {node.func.id} takes {arity} arguments")
+            for a in node.args:
+                walk(a, out)
+            out.append(name)
+        elif isinstance(node, ast.Subscript) and isinstance(node.value, ast.Name):
+            idx = node.slice
+            if not (isinstance(idx, ast.Constant) and isinstance(idx.value, int)):
+                raise ValueError("parse_expr: a component must be an integer literal")
+            out.append(("load", node.value.id, idx.value))
+        elif isinstance(node, ast.Name):
+            out.append(("load", node.id, 0))
+        elif isinstance(node, ast.Constant) and isinstance(node.value, (int, float)) \
+                and not isinstance(node.value, bool):
+            out.append(("const", float(node.value)))
+        else:
+            raise ValueError(f"parse_expr: unsupported syntax {ast.dump(node)[:60]}")
+        return out
+    return walk(ast.parse(text.strip(), mode="eval").body, [])
 
 
 class SoaxError(RuntimeError):
@@ -442,6 +485,33 @@ class Particles:
         co = (C.c_double * max(1, k))(*[float(t[1]) for t in terms])
         _check(lib().soax_lincomb(self.h, self.fidx(dst[0]), int(dst[1]), k, fs, cs, co, float(constant),
                                   _stream(stream)), "soax_lincomb")
+
+    def expr(self, dst, program, compute="f64", stream=None):
+        """soax_expr: dst = program, one pass over the planes involved.  dst is (field,
+        comp); program is a postfix list as parse_expr returns it (("load", field, comp),
+        ("const", value), operator names) or an infix string for parse_expr; compute is the
+        arithmetic type, "f32" or "f64"."""
+        prog = parse_expr(program) if isinstance(program, str) else program
+        ops = (soax_expr_op * max(1, len(prog)))()
+        for j, item in enumerate(prog):
+            name = item if isinstance(item, str) else item[0]
+            o = ops[j]
+            o.op = EXPR_OPS[name]
+            if name == "load":
+                o.field, o.comp = self.fidx(item[1]), int(item[2])
+            elif name == "const":
+                o.value = float(item[1])
+        _check(lib().soax_expr(self.h, self.fidx(dst[0]), int(dst[1]), ops, len(prog), DTYPES[compute],
+                               _stream(stream)), "soax_expr")
+
+    def assign(self, text, compute="f64", stream=None):
+        """Listing 5's notation: "pos[0] = vel[1] - vel[2]" (soax_expr of the right-hand side
+        into the left-hand plane)."""
+        lhs, rhs = text.split("=", 1)
+        dst = parse_expr(lhs)
+        if len(dst) != 1 or not isinstance(dst[0], tuple) or dst[0][0] != "load":
+            raise ValueError("assign: the left-hand side must be one field component")
+        self.expr((dst[0][1], dst[0][2]), parse_expr(rhs), compute, stream)
 
     def euler(self, dt, pos="x", vel="v", per_component=False, stream=None):
         """The paper's Eq. 1 step x += dt*v on f32 x 3 fields (fused, or one launch per

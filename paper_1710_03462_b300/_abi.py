@@ -26,6 +26,14 @@ class soax_tune(C.Structure):
                 ("fuse_steps", C.c_int32)]
 
 
+class soax_expr_op(C.Structure):
+    _fields_ = [("op", C.c_int32), ("field", C.c_int32), ("comp", C.c_int32), ("pad", C.c_int32),
+                ("value", C.c_double)]
+
+
+EXPR_OPS = {"load": 0, "const": 1, "add": 2, "sub": 3, "mul": 4, "div": 5, "neg": 6, "abs": 7, "sqrt": 8,
+            "min": 9, "max": 10, "fma": 11}
+
 _p, _i32, _i64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
 _P = C.POINTER
 
@@ -65,6 +73,7 @@ SIGNATURES = {
     "soax_sort_by_cell_noalloc": [_p, _i32, _p, _p],
     "soax_fill": [_p, _i32, C.c_double, _p],
     "soax_lincomb": [_p, _i32, _i32, _i32, _p, _p, _p, C.c_double, _p],
+    "soax_expr": [_p, _i32, _i32, _P(soax_expr_op), _i32, _i32, _p],
     "soax_euler": [_p, _i32, _i32, C.c_float, _i32, _p],
     "soax_euler_aos": [_p, _i64, _i64, _i64, _i64, C.c_float, _p],
     "soax_adjoint_workspace_bytes": [_p, _i32, _i32, _P(_sz)],

@@ -193,3 +193,29 @@ def test_workspace_sizes():
     assert L.soax_adjoint_workspace_bytes(h, 1000, 32, C.byref(b)) == 0
     assert b.value >= (32 + 32) * 36 * 1000
     L.soax_destroy(h)
+
+
+def test_expr_validation_without_gpu():
+    """soax_expr checks its program on the host before any launch (an empty set still
+    validates it)."""
+    L = sx.lib()
+    rc, h = _create(sx.WIDE_SCHEMA, 0)
+    assert rc == 0
+
+    def run(ops, dst=(1, 0), compute=4):
+        arr = (_abi.soax_expr_op * max(1, len(ops)))()
+        for j, (op, f, c, v) in enumerate(ops):
+            arr[j].op, arr[j].field, arr[j].comp, arr[j].value = op, f, c, v
+        return L.soax_expr(h, dst[0], dst[1], arr, len(ops), compute, None)
+    load_pos, const, add, fma = (0, 1, 0, 0.0), (1, 0, 0, 2.0), (2, 0, 0, 0.0), (11, 0, 0, 0.0)
+    assert run([load_pos, const, add]) == 0
+    assert run([load_pos, add]) == -1                   # underflow
+    assert run([load_pos, const]) == -1                 # two values left
+    assert run([load_pos, const, fma]) == -1            # fma needs three
+    assert run([(99, 0, 0, 0.0)]) == -1                 # unknown operation
+    assert run([load_pos], compute=0) == -1             # compute type
+    assert run([load_pos], dst=(5, 0)) == -2            # u8 destination
+    assert run([(0, 1, 3, 0.0)]) == -1                  # bad component
+    assert run([const] * 17 + [add] * 16) == -1         # deeper than 16
+    assert run([const] * 65) == -1                      # more than 64 operations
+    L.soax_destroy(h)
