@@ -74,7 +74,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="soax", choices=["soax", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
-    ap.add_argument("--only", choices=["euler", "adjoint", "batched", "aos", "fixed", "plain", "wide"],
+    ap.add_argument("--only", choices=["euler", "euler_sweep", "adjoint", "batched", "aos", "fixed", "plain", "wide"],
                     help="run only this secondary row (profiling captures)")
     ap.add_argument("--n", type=int, default=None, help="particles (default: the row's workload)")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="pieces per soax_step_host call in the e2e loop")
@@ -83,6 +83,7 @@ def parse_args(argv=None):
     ap.add_argument("--nens", type=int, default=None, help="--only batched: the first NENS ensembles")
     ap.add_argument("--fixed-tune", action="store_true", help="--only batched: a fixed launch shape, no autotuning")
     ap.add_argument("--intervals", type=int, default=None, help="--only wide: sort intervals to time")
+    ap.add_argument("--sizes", type=int, nargs="*", default=None, help="--only euler: AoS_SIZE record sizes")
     ap.add_argument("--nsteps", type=int, nargs="*", default=None,
                     help="--only fixed: steps per launch (default 10 and 20)")
     return ap.parse_args(argv)
@@ -559,7 +560,7 @@ def _time(torch, fn, reps=1):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
-def euler_replica(sx, torch, n, dev):
+def euler_replica(sx, torch, n, dev, sizes=(0, 32)):
     """The paper's experiment on B300 (Sec. 2-3): Eq. 1 in single precision on SoA planes
     (fused; and one launch per component, as the paper's GPU code) and on Listing 4's
     AoS_SIZE records; time per particle and the AoS/SoA ratios the paper reports."""
@@ -576,7 +577,7 @@ def euler_replica(sx, torch, n, dev):
     out["roofline"] = hbm_roofline(36, n, t_fused)
     out["soa_per_component_ns_per_particle"] = t_comp / n * 1e9
     del q
-    for size in (0, 32):
+    for size in sizes:
         rb = 24 + 4 * size
         rec = torch.empty(n * rb // 4, dtype=torch.float32, device=dev).normal_()
         t_aos = _time(torch, lambda: sx.euler_aos(rec, n, rb, 0, 12, 1e-3), reps=10)
@@ -585,6 +586,49 @@ def euler_replica(sx, torch, n, dev):
         del rec
     torch.cuda.empty_cache()
     return out
+
+
+def euler_sweep(sx, torch, dev, ns=None, sizes=(0, 1, 2, 4, 8, 16, 32), max_bytes=48 << 30):
+    """The paper's GPU experiment (Sec. 3.2, Figs. of the M2050 benchmark) on B300: the
+    single-precision Euler step x += dt*v (Eq. 1) for N from 1e2 to 1e9 particles, on SoA
+    planes (one fused launch over all components, and the paper's three launches, one per
+    component) and on Listing 4's AoS_SIZE records for SIZE in sizes (24 + 4 SIZE bytes;
+    sizes whose buffer would exceed max_bytes are skipped at that N).  Each form is timed
+    per step with CUDA events over a CUDA graph of many steps (kernel time, as the paper
+    measured with the profiler), in ns per particle; the ratios AoS_SIZE / SoA (the
+    paper's three-launch SoA) and the smallest N from which SoA is ahead of AoS_0."""
+    ns = ns or [100, 300, 1000, 2000, 5000, 10000, 100000, 1000000, 10000000, 100000000, 1000000000]
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for n in ns:
+        reps = max(2, min(200, int(2e8 // max(n, 1))))
+        row = {"n": n, "steps_per_graph": reps}
+        q = sx.Particles([("x", "f32", 3, "P"), ("v", "f32", 3, "V")], n, device=dev, shadow=False)
+        for name in ("x", "v"):
+            for t in q.field(name):
+                t.normal_()
+        for key, fn in (("soa_fused", lambda s: q.euler(1e-3, stream=s)),
+                        ("soa_per_component", lambda s: q.euler(1e-3, per_component=True, stream=s))):
+            g = _graph(torch, dev, lambda s: [fn(s) for _ in range(reps)])
+            row[key + "_ns"] = _events(torch, stream, g.replay, reps=3) / reps / n * 1e9
+            del g
+        del q
+        for size in sizes:
+            rb = 24 + 4 * size
+            if n * rb > max_bytes:
+                continue
+            rec = torch.empty(n * rb // 4, dtype=torch.float32, device=dev).normal_()
+            g = _graph(torch, dev, lambda s: [sx.euler_aos(rec, n, rb, 0, 12, 1e-3, stream=s) for _ in range(reps)])
+            row[f"aos{size}_ns"] = _events(torch, stream, g.replay, reps=3) / reps / n * 1e9
+            row[f"aos{size}_over_soa"] = row[f"aos{size}_ns"] / row["soa_per_component_ns"]
+            del g, rec
+        row["soa_fused_GB/s"] = 36 / row["soa_fused_ns"]
+        rows.append(row)
+        torch.cuda.empty_cache()
+    cross = next((r["n"] for r in rows if r.get("aos0_ns", 0) > r["soa_per_component_ns"]), None)
+    cross_fused = next((r["n"] for r in rows if r.get("aos0_ns", 0) > r["soa_fused_ns"]), None)
+    return {"rows": rows, "sizes": list(sizes), "units": "ns per particle per step (kernel time, CUDA graph)",
+            "soa3_ahead_of_aos0_from_n": cross, "soa_fused_ahead_of_aos0_from_n": cross_fused}
 
 
 def issue_peak(torch, dev):
@@ -953,7 +997,9 @@ def run_only(args):
     import paper_1710_03462_b300 as sx
     dev = torch.device("cuda", torch.cuda.current_device())
     if args.only == "euler":
-        row = euler_replica(sx, torch, args.n or WL["n"], dev)
+        row = euler_replica(sx, torch, args.n or WL["n"], dev, sizes=args.sizes or (0, 32))
+    elif args.only == "euler_sweep":
+        row = euler_sweep(sx, torch, dev, ns=[args.n] if args.n else None)
     elif args.only == "adjoint":
         row = row_adjoint(sx, torch, dev, args.n)
     elif args.only == "batched":

@@ -266,13 +266,13 @@ _EXPR_OPS = {"load": 0, "const": 1, "add": 2, "sub": 3, "mul": 4, "div": 5, "neg
              "min": 9, "max": 10, "fma": 11}
 
 
-def expr(program, compute="f64", out_dtype=np.float64):
+def expr(program, compute="f64", out_dtype=np.float64, n=None):
     """Evaluate a postfix program element by element (orc_expr).  program: a list of
     ("load", array), ("const", value) or an operator name (add, sub, mul, div, neg, abs,
-    sqrt, min, max, fma); compute: "f32" or "f64"; every loaded array has the same length.
-    Returns the result array of out_dtype (float32 or float64)."""
+    sqrt, min, max, fma); compute: "f32" or "f64"; every loaded array has n elements (n
+    may be omitted when the program loads an array).  Returns the result array of
+    out_dtype (float32 or float64)."""
     ops, vals, srcs, codes, keep = [], [], [], [], []
-    n = None
     for item in program:
         name, arg = (item, None) if isinstance(item, str) else item
         ops.append(_EXPR_OPS[name])

@@ -78,7 +78,7 @@ def test_random_programs(n, compute):
         dst = ("pos", t % 3) if t % 2 == 0 else ("acc", t % 3)
         p.expr(dst, prog, compute)
         got = p.numpy()[dst[0]][dst[1]]
-        want = oracle.expr(_oracle_program(prog, d), compute, got.dtype)
+        want = oracle.expr(_oracle_program(prog, d), compute, got.dtype, n=n)
         assert _same(got, want), prog
         d[dst[0]][dst[1]] = got  # the next program may read it
 
