@@ -3,9 +3,9 @@
 // the candidate launch shapes and returns the fastest.
 //
 // The ensembles are cut into tiles of block*PPT particles; tile t belongs to the
-// ensemble e with prefix[e] <= t < prefix[e+1] (binary search over the prefix).  A grid
-// sized to fill the GPU once walks the tiles with a fixed stride, so no block waits on
-// another.  Two forms: one launch per step, with soax_step's per-particle function, and
+// ensemble e with prefix[e] <= t < prefix[e+1].  A grid sized to fill the GPU once walks
+// the tiles (the per-step form: each block an equal contiguous range of them; the fused
+// form: a fixed stride), so no block waits on another.  Two forms: one launch per step, with soax_step's per-particle function, and
 // the fused form (tune.fuse_steps), all steps of the call in registers with
 // soax_step_fused's per-particle function.  Every launch shape of a form gives the same
 // bits as the matching single-ensemble call.
@@ -52,30 +52,52 @@ __device__ __forceinline__ bool plan_ok(const PlanHeader* hdr, int nens, int64_t
   return ok;
 }
 
-template <int PPT, int VB>
-__global__ void __launch_bounds__(512) k_step_batched(const PlanHeader* __restrict__ hdr,
+// One launch per step.  Each block takes a contiguous range of tiles (an equal share of
+// all of them), so it stays within one ensemble for long stretches: it finds the
+// ensemble of its first tile once, steps to the next ensemble when its tiles run out, and
+// only then reloads the ensemble's arguments and rebuilds the three amplitude-scaled
+// sin/cos tables (96 KB of dynamic shared memory) -- the tables and per-particle
+// function of soax_step, hence its bits.  PLAIN: no ensemble has a tau or acceleration
+// field (one per-particle form, fewer registers); otherwise the form is chosen per
+// ensemble.
+template <int PPT, int VB, bool PLAIN>
+__global__ void __launch_bounds__(512, 2) k_step_batched(const PlanHeader* __restrict__ hdr,
                                                       const EnsArgs* __restrict__ ens,
                                                       const int64_t* __restrict__ prefix, int nens, int64_t ntiles,
                                                       FlowK f, int nsteps_inner, int* status) {
-  extern __shared__ int64_t s_prefix[];
-  __shared__ float4 s_tab[SOAX_TRIG_TABLE_SIZE];
+  extern __shared__ float4 s_tab3[];
+  __shared__ EnsArgs s_e;
   const int64_t tile_parts = (int64_t)blockDim.x * PPT;
   if (!plan_ok(hdr, nens, ntiles, tile_parts, status)) return;
-  for (int k = threadIdx.x; k <= nens; k += blockDim.x) s_prefix[k] = prefix[k];
-  load_trig_table(s_tab);
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int lo = 0, hi = nens;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (s_prefix[mid] <= t) lo = mid; else hi = mid;
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * per;
+  const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
+  if (t0 >= t1) return;  // uniform over the block
+  int lo = 0, hi = nens;  // the ensemble of t0: prefix[lo] <= t0 < prefix[lo + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t0) lo = mid; else hi = mid;
+  }
+  int cur = -1;
+  int64_t next = 0;  // prefix[lo + 1] while lo == cur
+  for (int64_t t = t0; t < t1; ++t) {
+    if (cur < 0 || t >= next) {  // uniform over the block, as t is
+      while (prefix[lo + 1] <= t) ++lo;
+      __syncthreads();  // every thread is done with the previous ensemble's tables
+      if (threadIdx.x == 0) s_e = ens[lo];
+      load_scaled_trig_tables(s_tab3, ff_from2(ens[lo].Af), ff_from2(ens[lo].Bf), ff_from2(ens[lo].Cf));
+      cur = lo;
+      next = prefix[lo + 1];
     }
-    const EnsArgs e = ens[lo];
-    const int64_t i0 = (t - s_prefix[lo]) * tile_parts + (int64_t)threadIdx.x * PPT;
+    const EnsArgs& e = s_e;
+    const int64_t i0 = (t - prefix[cur]) * tile_parts + (int64_t)threadIdx.x * PPT;
     if (i0 < e.n) {
       const StepC kc = make_stepc(e, f);
-      const TrigUnscaled tg = trig_unscaled(s_tab, e);
+      const TrigScaled tg{s_tab3};
       const int64_t cnt = e.n - i0;
-      if (e.tau_src) {
+      if constexpr (PLAIN) {
+        step_span_t<PPT, VB, false, false>(e, kc, tg, i0, cnt, nsteps_inner);
+      } else if (e.tau_src) {
         if (e.ax) step_span_t<PPT, VB, true, true>(e, kc, tg, i0, cnt, nsteps_inner);
         else step_span_t<PPT, VB, true, false>(e, kc, tg, i0, cnt, nsteps_inner);
       } else {
@@ -166,11 +188,16 @@ using BatchedKernel = void (*)(const PlanHeader*, const EnsArgs*, const int64_t*
 using BatchedFusedKernel = void (*)(const PlanHeader*, const EnsArgs*, const int64_t*, int, int64_t, FlowK, TurnsK,
                                     int, int*);
 
-static BatchedKernel pick_kernel(int ppt, int vb) {
-  if (ppt == 1) return k_step_batched<1, 64>;
-  if (ppt == 2) return vb == 128 ? k_step_batched<2, 128> : k_step_batched<2, 64>;
-  if (ppt == 4) return vb == 128 ? k_step_batched<4, 128> : k_step_batched<4, 64>;
+template <bool PLAIN>
+static BatchedKernel pick_kernel_form(int ppt, int vb) {
+  if (ppt == 1) return k_step_batched<1, 64, PLAIN>;
+  if (ppt == 2) return vb == 128 ? k_step_batched<2, 128, PLAIN> : k_step_batched<2, 64, PLAIN>;
+  if (ppt == 4) return vb == 128 ? k_step_batched<4, 128, PLAIN> : k_step_batched<4, 64, PLAIN>;
   return nullptr;
+}
+
+static BatchedKernel pick_kernel(int ppt, int vb, int form) {
+  return form == 0 ? pick_kernel_form<true>(ppt, vb) : pick_kernel_form<false>(ppt, vb);
 }
 
 template <int FORM>
@@ -280,13 +307,13 @@ static int prepare(const soax_t* hs, const soax_flow* fls, int nens, const soax_
       e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return cuda_fail(e, "soax_step_batched: fused kernel attributes");
   } else {
-    out->kern = pick_kernel(t.parts_per_thread, t.vec_bits);
-    out->smem = (size_t)(nens + 1) * sizeof(int64_t);
+    out->kern = pick_kernel(t.parts_per_thread, t.vec_bits, form);
+    out->smem = kScaledTrigBytes;
     fn = (const void*)out->kern;
-    if (out->smem > 16 * 1024) {  // plus 32 KB of static shared memory (the sin/cos table)
-      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
-      if (e != cudaSuccess) return cuda_fail(e, "soax_step_batched: smem attribute");
-    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out->smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return cuda_fail(e, "soax_step_batched: kernel attributes");
   }
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, t.block, out->smem);
   if (e != cudaSuccess || per_sm < 1) per_sm = 1;
