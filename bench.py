@@ -39,6 +39,7 @@ import hashlib
 import glob
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -136,11 +137,28 @@ def unit_sources(unit):
     return sorted(seen) + [os.path.join(ROOT, "paper_1710_03462_b300", "build.py")]
 
 
+def code_only(text):
+    """A source without its comments and blank lines: what the compiler sees (the
+    counters of a kernel depend on its code, not on the words around it)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    lines = []
+    for line in text.splitlines():
+        if line.lstrip().startswith("#") and not line.lstrip().startswith(("#include", "#define", "#pragma", "#if",
+                                                                            "#else", "#endif", "#ifdef", "#ifndef")):
+            line = ""  # a Python comment line (the build script)
+        line = re.sub(r"//.*$", "", line).rstrip()
+        if line:
+            lines.append(line)
+    return "\n".join(lines)
+
+
 def source_hash(unit):
+    """Hash of the code (comments dropped) of a kernel's translation unit, its headers and
+    the build script."""
     h = hashlib.sha1()
     for f in unit_sources(unit):
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8", errors="replace") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -299,7 +299,7 @@ int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_
  * linking the library with no device allocator of their own, or time-step loops that
  * forbid cudaMalloc because it can synchronise the device and breaks a memory budget
  * fixed at start-up.  Same keys, radix sort and permute-gather as soax_sort_by_cell,
- * with the scratch in a static device array of 22 MiB that every GPU loading the
+ * with the scratch in a static device array of 32 MiB that every GPU loading the
  * library holds until exit; this call allocates nothing.  Limits: n <= 1048576 and
  * grid in 1..64 (SOAX_EINVAL otherwise, before any device work).  perm_out: n u32 on
  * the device receiving the permutation, or NULL.  The first call on a device looks up

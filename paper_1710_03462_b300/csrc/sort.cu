@@ -124,10 +124,13 @@ CellKeyK make_cell_key_k(int grid) {
 }
 
 // ------------------------------------------------------------------ radix passes
+// gate: NULL, or a device flag; the radix kernels return at once while it is 0 (the cell
+// counting sort below has done the work).
 __global__ void __launch_bounds__(kSortBlock) k_radix_upsweep(const uint32_t* __restrict__ keys, int64_t n, int shift,
                                                               uint32_t mask, int64_t nblocks,
                                                               uint32_t* __restrict__ counts,
-                                                              uint32_t* __restrict__ totals) {
+                                                              uint32_t* __restrict__ totals, const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ uint32_t hist[kMaxRadix];
   const int radix = (int)mask + 1, tid = threadIdx.x, lane = tid & 31;
   for (int d = tid; d < radix; d += kSortBlock) hist[d] = 0;
@@ -159,7 +162,8 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_upsweep(const uint32_t* __
 // One block per digit d: counts[d][b] <- sum_{d' < d} totals[d'] + sum_{b' < b} counts[d][b'].
 __global__ void __launch_bounds__(kScanThreads) k_radix_scan_rows(uint32_t* __restrict__ counts,
                                                                   const uint32_t* __restrict__ totals,
-                                                                  int64_t nblocks) {
+                                                                  int64_t nblocks, const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ uint32_t scratch[33];
   const int d = blockIdx.x, tid = threadIdx.x;
   uint32_t part = 0;
@@ -183,7 +187,8 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scan_rows(uint32_t* __re
 __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n, int shift, uint32_t mask, int64_t nblocks,
-    const uint32_t* __restrict__ counts, int* __restrict__ status) {
+    const uint32_t* __restrict__ counts, int* __restrict__ status, const int* gate) {
+  if (gate && *gate == 0) return;
   extern __shared__ uint32_t sm[];
   const int radix = (int)mask + 1;
   uint32_t* wc = sm;                         // [warps][radix]: per-warp digit counts, then prefixes
@@ -335,6 +340,226 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArg
   }
 }
 
+// ------------------------------------------------------------------ cell counting sort
+// The stable argsort of cell keys of at most 18 bits (grids up to 64^3) in one pass over
+// the keys plus per-cell work, for keys that come in near cell order (the keys of the
+// particles a previous sort left in cell order, after a few steps).  Every aligned
+// 32-key segment of the input is cut into groups of equal keys (one warp match):
+//   count:   per key d, its particle count m_d and its number of groups C_d;
+//   scan:    bucket starts (exclusive sums of m) and group-record starts (of C);
+//   scatter: each group reserves cnt consecutive slots of its key's bucket (one atomic)
+//            and writes its indices there in lane order, and a record (segment, first
+//            slot, cnt) into its key's record range;
+//   order:   one warp per key: the bucket's groups come from distinct segments, i.e.
+//            disjoint ascending index ranges, so the stable order of the bucket is its
+//            groups ranked by segment; each group's destination is the count of the
+//            bucket's particles in groups of smaller segment, and one pass moves every
+//            index there.
+// A key with more than kCellMaxParticles particles or kCellMaxGroups groups does not fit
+// the order kernel's per-warp buffers: the scan then raises the gate and the radix passes
+// (launched after, gated) sort instead; scatter and order return at once.  Nothing waits
+// on another block.
+constexpr int kCellMaxParticles = 2048;  // per key, for the per-warp shift table (int16)
+constexpr int kCellMaxGroups = 256;      // per key: 8 group records per lane
+constexpr int kCellChunk = 4096;         // keys per scan block
+constexpr int kCellBlock = 256;
+constexpr int kCellOrderWarps = 8;
+
+struct CellSortArgs {
+  const uint32_t* keys;
+  int64_t n;
+  uint32_t mask;           // 2^bits - 1; keys are taken modulo 2^bits, as the radix sort does
+  int nb;                  // 2^bits buckets
+  uint32_t* cnt;           // [nb] particle counts, then the slot cursors
+  uint32_t* grp;           // [nb] group counts, then the record cursors
+  uint32_t* start;         // [nb + 1] bucket starts
+  uint32_t* gstart;        // [nb + 1] record starts
+  uint32_t* chunk_tot;     // [2 * nchunks] particle and group totals of each 4096-key chunk
+  int* gate;               // 0: this sort's result stands; 1: the radix passes sort
+  uint32_t* tmp;           // [n] indices in bucket order, unordered within a bucket
+  unsigned long long* rec; // [n] group records
+  uint32_t* perm;          // [n] the stable argsort
+  uint32_t* skeys;         // [n] sorted keys, or NULL
+  int* status;             // device status word: a record that points outside its bucket
+};
+
+__device__ __forceinline__ unsigned long long cell_rec(uint64_t seg, uint32_t slot, uint32_t cnt) {
+  return (seg << 36) | ((uint64_t)slot << 5) | (uint64_t)(cnt - 1);
+}
+
+__global__ void __launch_bounds__(kCellBlock) k_cell_count(const __grid_constant__ CellSortArgs a) {
+  extern __shared__ uint32_t s_tot[];  // [2 * nchunks]
+  const int nchunks = (a.nb + kCellChunk - 1) / kCellChunk;
+  for (int k = threadIdx.x; k < 2 * nchunks; k += blockDim.x) s_tot[k] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1;
+  const int64_t nseg = (a.n + 31) / 32;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sg = w0; sg < nseg; sg += wstride) {
+    const int64_t i = sg * 32 + lane;
+    const uint32_t d = i < a.n ? (a.keys[i] & a.mask) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (d != 0xFFFFFFFFu && (peers & lt) == 0) {
+      const uint32_t c = (uint32_t)__popc(peers);
+      atomicAdd(&a.cnt[d], c);
+      atomicAdd(&a.grp[d], 1u);
+      atomicAdd(&s_tot[2 * (d / kCellChunk)], c);
+      atomicAdd(&s_tot[2 * (d / kCellChunk) + 1], 1u);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * nchunks; k += blockDim.x)
+    if (s_tot[k]) atomicAdd(&a.chunk_tot[k], s_tot[k]);
+}
+
+// One block of kScanThreads per 4096 keys: bucket and record starts, the cursors, and
+// the gate for keys beyond the order kernel's capacity.
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan(const __grid_constant__ CellSortArgs a) {
+  __shared__ uint32_t scratch[33];
+  __shared__ uint32_t s_base[2];
+  const int c = blockIdx.x, tid = threadIdx.x;
+  if (tid < 2) {
+    uint32_t b = 0;
+    for (int k = 0; k < c; ++k) b += a.chunk_tot[2 * k + tid];
+    s_base[tid] = b;
+  }
+  __syncthreads();
+  const int b0 = c * kCellChunk + tid * 4;
+  uint32_t m[4], g[4], sm = 0, sg = 0;
+  bool big = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int b = b0 + j;
+    m[j] = b < a.nb ? a.cnt[b] : 0u;
+    g[j] = b < a.nb ? a.grp[b] : 0u;
+    big |= m[j] > (uint32_t)kCellMaxParticles || g[j] > (uint32_t)kCellMaxGroups;
+    sm += m[j];
+    sg += g[j];
+  }
+  uint32_t tm, tg;
+  uint32_t em = block_excl_scan(sm, scratch, &tm) + s_base[0];
+  uint32_t eg = block_excl_scan(sg, scratch, &tg) + s_base[1];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int b = b0 + j;
+    if (b < a.nb) {
+      a.start[b] = em;
+      a.gstart[b] = eg;
+      a.cnt[b] = em;  // the slot cursor
+      a.grp[b] = eg;  // the record cursor
+    }
+    em += m[j];
+    eg += g[j];
+  }
+  if (c == gridDim.x - 1 && tid == blockDim.x - 1) {
+    a.start[a.nb] = em;
+    a.gstart[a.nb] = eg;
+  }
+  if (big) atomicExch(a.gate, 1);
+}
+
+__global__ void __launch_bounds__(kCellBlock) k_cell_scatter(const __grid_constant__ CellSortArgs a) {
+  if (*a.gate) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1;
+  const int64_t nseg = (a.n + 31) / 32;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sg = w0; sg < nseg; sg += wstride) {
+    const int64_t i = sg * 32 + lane;
+    const uint32_t d = i < a.n ? (a.keys[i] & a.mask) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t slot = 0;
+    if (d != 0xFFFFFFFFu && lane == leader) {
+      const uint32_t c = (uint32_t)__popc(peers);
+      slot = atomicAdd(&a.cnt[d], c);
+      const uint32_t r = atomicAdd(&a.grp[d], 1u);
+      a.rec[r] = cell_rec((uint64_t)sg, slot, c);
+    }
+    slot = __shfl_sync(0xFFFFFFFFu, slot, leader);
+    if (d != 0xFFFFFFFFu) a.tmp[slot + __popc(peers & lt)] = (uint32_t)i;
+  }
+}
+
+// One warp per key (warps stride over the keys).  K: group records per lane (C <= 32 K).
+template <int K>
+__device__ __forceinline__ void cell_order_bucket(const CellSortArgs& a, uint32_t st, uint32_t m, uint32_t g0,
+                                                  uint32_t C, int16_t* shift) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long r[K];
+  uint32_t dest[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t q = (uint32_t)k * 32 + lane;
+    r[k] = q < C ? a.rec[g0 + q] : ~0ull;
+    dest[k] = 0;
+  }
+  // dest = the particles in groups of smaller segment (segments are distinct per key).
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    for (int sl = 0; sl < 32; ++sl) {
+      const unsigned long long o = __shfl_sync(0xFFFFFFFFu, r[k], sl);
+      const uint32_t oc = (uint32_t)(o & 31) + 1;
+      const bool valid = (uint32_t)k * 32 + sl < C;
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (valid && (o >> 36) < (r[j] >> 36)) dest[j] += oc;
+    }
+  }
+  // Only a workspace overwritten while the sort runs can hold a record outside its
+  // bucket: such a record is skipped, a destination outside the bucket clamped, and
+  // SOAX_EINVAL recorded (a wrong order, no access out of bounds).
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if ((uint32_t)k * 32 + lane < C) {
+      const uint32_t off = (uint32_t)((r[k] >> 5) & 0x7FFFFFFFu) - st;
+      const uint32_t cnt = (uint32_t)(r[k] & 31) + 1;
+      const int16_t sh = (int16_t)((int32_t)dest[k] - (int32_t)off);
+      if (off < m && cnt <= m - off)
+        for (uint32_t t = 0; t < cnt; ++t) shift[off + t] = sh;
+      else
+        bad = true;
+    }
+  }
+  __syncwarp();
+  for (uint32_t j = lane; j < m; j += 32) {
+    const int32_t q = (int32_t)j + shift[j];
+    bad |= q < 0 || q >= (int32_t)m;
+    a.perm[st + (uint32_t)min(max(q, 0), (int32_t)m - 1)] = a.tmp[st + j];
+  }
+  if (bad) atomicExch(a.status, (int)SOAX_EINVAL);
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kCellOrderWarps * 32) k_cell_order(const __grid_constant__ CellSortArgs a) {
+  if (*a.gate) return;
+  __shared__ int16_t s_shift[kCellOrderWarps][kCellMaxParticles];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t wstride = (int64_t)gridDim.x * kCellOrderWarps;
+  for (int64_t d = (int64_t)blockIdx.x * kCellOrderWarps + w; d < a.nb; d += wstride) {
+    const uint32_t st = a.start[d], m = a.start[d + 1] - st;
+    if (m == 0) continue;
+    if (a.skeys)
+      for (uint32_t j = lane; j < m; j += 32) a.skeys[st + j] = (uint32_t)d;
+    const uint32_t g0 = a.gstart[d], C = a.gstart[d + 1] - g0;
+    if (C == 1) {  // one group: already in order
+      for (uint32_t j = lane; j < m; j += 32) a.perm[st + j] = a.tmp[st + j];
+    } else if (C <= 32) {
+      cell_order_bucket<1>(a, st, m, g0, C, s_shift[w]);
+    } else if (C <= 64) {
+      cell_order_bucket<2>(a, st, m, g0, C, s_shift[w]);
+    } else if (C <= 128) {
+      cell_order_bucket<4>(a, st, m, g0, C, s_shift[w]);
+    } else {
+      cell_order_bucket<8>(a, st, m, g0, C, s_shift[w]);
+    }
+  }
+}
+
 static int key_bits_for_grid(int G) {
   uint32_t maxkey = (uint32_t)G * G * G - 1;
   int b = 0;
@@ -345,7 +570,15 @@ static int key_bits_for_grid(int G) {
 struct SortWs {
   size_t off_keys, off_skeys, off_perm, off_radix, total;
   RadixPlan rp;
+  // The cell counting sort (grids up to 64^3): its zeroed header (gate, counts, chunk
+  // totals), bucket and record starts, and its index and record arrays, which share the
+  // radix region (the radix passes only run, gated, after the counting sort is done).
+  bool cell = false;
+  int bits = 0, nb = 0, nchunks = 0;
+  size_t off_hdr = 0, hdr_bytes = 0, off_start = 0, off_gstart = 0, off_tmp = 0, off_rec = 0;
 };
+
+constexpr int kCellMaxBits = 18;
 
 static SortWs sort_ws_plan(int64_t n, int G) {
   SortWs w;
@@ -356,9 +589,29 @@ static SortWs sort_ws_plan(int64_t n, int G) {
   off = align256(off + (size_t)n * 4);
   w.off_perm = off;
   off = align256(off + (size_t)n * 4);
+  w.bits = key_bits_for_grid(G);
+  w.rp = radix_plan(n, w.bits);
+  w.cell = w.bits <= kCellMaxBits;
+  if (w.cell) {
+    w.nb = 1 << w.bits;
+    w.nchunks = (w.nb + kCellChunk - 1) / kCellChunk;
+    w.off_hdr = off;  // gate (256 B), cnt[nb], grp[nb], chunk totals[2 nchunks]
+    w.hdr_bytes = 256 + (size_t)w.nb * 8 + (size_t)w.nchunks * 8;
+    off = align256(off + w.hdr_bytes);
+    w.off_start = off;
+    off = align256(off + (size_t)(w.nb + 1) * 4);
+    w.off_gstart = off;
+    off = align256(off + (size_t)(w.nb + 1) * 4);
+  }
   w.off_radix = off;
-  w.rp = radix_plan(n, key_bits_for_grid(G));
-  w.total = off + w.rp.total;
+  size_t tail = w.rp.total;
+  if (w.cell) {
+    w.off_tmp = off;
+    w.off_rec = align256(off + (size_t)n * 4);
+    const size_t cell_tail = w.off_rec + (size_t)n * 8 - off;
+    if (cell_tail > tail) tail = cell_tail;
+  }
+  w.total = off + tail;
   return w;
 }
 
@@ -397,9 +650,21 @@ extern "C" int soax_radix_workspace_bytes(int64_t n, int32_t key_bits, size_t* b
   return SOAX_OK;
 }
 
+namespace soax {
+static int radix_sort_gated(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                            int64_t n, int32_t key_bits, void* ws, size_t ws_bytes, void* stream, const int* gate);
+}  // namespace soax
+
 extern "C" int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                                      uint32_t* vals_out, int64_t n, int32_t key_bits, void* ws, size_t ws_bytes,
                                      void* stream) {
+  return soax::radix_sort_gated(keys_in, vals_in, keys_out, vals_out, n, key_bits, ws, ws_bytes, stream, nullptr);
+}
+
+namespace soax {
+// The radix sort; gate as for the kernels (NULL: always sort).
+static int radix_sort_gated(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                            int64_t n, int32_t key_bits, void* ws, size_t ws_bytes, void* stream, const int* gate) {
   if (n < 0 || n >= (int64_t(1) << 31)) return fail(SOAX_EINVAL, "soax_radix_sort_pairs: n out of range");
   if (key_bits < 1 || key_bits > 32) return fail(SOAX_EINVAL, "soax_radix_sort_pairs: key_bits in 1..32");
   if (n == 0) return SOAX_OK;
@@ -443,16 +708,18 @@ extern "C" int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* va
     uint32_t* vout = last ? vals_out : av[pass & 1];
     cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)radix * 4, s);
     if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: memset");
-    k_radix_upsweep<<<(unsigned)p.nblocks, kSortBlock, 0, s>>>(kin, n, shift, mask, p.nblocks, counts, totals);
+    k_radix_upsweep<<<(unsigned)p.nblocks, kSortBlock, 0, s>>>(kin, n, shift, mask, p.nblocks, counts, totals, gate);
     if (int r = check_launch("radix upsweep")) return r;
-    k_radix_scan_rows<<<radix, kScanThreads, 0, s>>>(counts, totals, p.nblocks);
+    k_radix_scan_rows<<<radix, kScanThreads, 0, s>>>(counts, totals, p.nblocks, gate);
     if (int r = check_launch("radix scan")) return r;
     k_radix_downsweep<<<(unsigned)p.nblocks, kSortBlock, downsweep_smem(radix), s>>>(kin, vin, kout, vout, n, shift,
-                                                                                    mask, p.nblocks, counts, status);
+                                                                                    mask, p.nblocks, counts, status,
+                                                                                    gate);
     if (int r = check_launch("radix downsweep")) return r;
   }
   return SOAX_OK;
 }
+}  // namespace soax
 
 namespace soax {
 
@@ -526,16 +793,66 @@ extern "C" int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_byt
   return SOAX_OK;
 }
 
-// The radix sort of the given keys and the permute-gather (soax_sort_by_cell after its
-// key pass).  keys may lie in the workspace's own key region.
+namespace soax {
+
+// The stable argsort of n cell keys on a grid^3 grid into perm (and the sorted keys into
+// skeys unless NULL), in the workspace laid out by sort_ws_plan: the cell counting sort
+// for grids up to 64^3 (the radix passes, gated, behind it for keys it cannot take), the
+// radix sort alone beyond.
+static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, int64_t n, int grid, void* ws,
+                        void* stream) {
+  const SortWs w = sort_ws_plan(n, grid);
+  char* base = static_cast<char*>(ws);
+  if (!w.cell)
+    return radix_sort_gated(keys, nullptr, skeys, perm, n, w.bits, base + w.off_radix, w.rp.total, stream, nullptr);
+  if (!aligned16(keys)) return fail(SOAX_EALIGN, "cell sort: keys not 16-byte aligned");
+  CellSortArgs a;
+  a.keys = keys;
+  a.n = n;
+  a.mask = (uint32_t)(w.nb - 1);
+  a.nb = w.nb;
+  a.gate = reinterpret_cast<int*>(base + w.off_hdr);
+  a.cnt = reinterpret_cast<uint32_t*>(base + w.off_hdr + 256);
+  a.grp = a.cnt + w.nb;
+  a.chunk_tot = a.grp + w.nb;
+  a.start = reinterpret_cast<uint32_t*>(base + w.off_start);
+  a.gstart = reinterpret_cast<uint32_t*>(base + w.off_gstart);
+  a.tmp = reinterpret_cast<uint32_t*>(base + w.off_tmp);
+  a.rec = reinterpret_cast<unsigned long long*>(base + w.off_rec);
+  a.perm = perm;
+  a.skeys = skeys;
+  a.status = status_word();
+  if (!a.status) return fail(SOAX_ECUDA, "cell sort: status word");
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemsetAsync(base + w.off_hdr, 0, w.hdr_bytes, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cell sort: memset");
+  const int64_t seg_blocks = ((n + 31) / 32 + kCellBlock / 32 - 1) / (kCellBlock / 32);
+  const size_t count_smem = (size_t)w.nchunks * 8;
+  const int gc = persistent_grid((const void*)k_cell_count, kCellBlock, count_smem, seg_blocks);
+  k_cell_count<<<gc, kCellBlock, count_smem, s>>>(a);
+  if (int r = check_launch("cell sort: count")) return r;
+  k_cell_scan<<<w.nchunks, kScanThreads, 0, s>>>(a);
+  if (int r = check_launch("cell sort: scan")) return r;
+  const int gs = persistent_grid((const void*)k_cell_scatter, kCellBlock, 0, seg_blocks);
+  k_cell_scatter<<<gs, kCellBlock, 0, s>>>(a);
+  if (int r = check_launch("cell sort: scatter")) return r;
+  const int go = persistent_grid((const void*)k_cell_order, kCellOrderWarps * 32, 0,
+                                 (w.nb + kCellOrderWarps - 1) / kCellOrderWarps);
+  k_cell_order<<<go, kCellOrderWarps * 32, 0, s>>>(a);
+  if (int r = check_launch("cell sort: order")) return r;
+  return radix_sort_gated(keys, nullptr, skeys, perm, n, w.bits, base + w.off_radix, w.rp.total, stream, a.gate);
+}
+
+}  // namespace soax
+
+// The sort of the given keys and the permute-gather (soax_sort_by_cell after its key
+// pass).  keys may lie in the workspace's own key region.
 static int sort_by_keys_impl(soax_t h, int32_t grid, const uint32_t* keys, void* ws, void* stream) {
   const SortWs w = sort_ws_plan(h->n, grid);
   char* base = static_cast<char*>(ws);
   uint32_t* skeys = reinterpret_cast<uint32_t*>(base + w.off_skeys);
   uint32_t* perm = reinterpret_cast<uint32_t*>(base + w.off_perm);
-  if (int r = soax_radix_sort_pairs(keys, nullptr, skeys, perm, h->n, key_bits_for_grid(grid), base + w.off_radix,
-                                    w.rp.total, stream))
-    return r;
+  if (int r = cell_argsort(keys, skeys, perm, h->n, grid, ws, stream)) return r;
   return soax_permute(h, perm, stream);
 }
 
@@ -550,8 +867,7 @@ extern "C" int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void
   if (!ws || ws_bytes < w.total) return fail(SOAX_ENOMEM, "soax_sort_perm: workspace too small");
   if (!aligned16(ws)) return fail(SOAX_EALIGN, "soax_sort_perm: workspace not 16-byte aligned");
   char* base = static_cast<char*>(ws);
-  return soax_radix_sort_pairs(keys, nullptr, nullptr, reinterpret_cast<uint32_t*>(base + w.off_perm), h->n,
-                               key_bits_for_grid(grid), base + w.off_radix, w.rp.total, stream);
+  return cell_argsort(keys, nullptr, reinterpret_cast<uint32_t*>(base + w.off_perm), h->n, grid, ws, stream);
 }
 
 extern "C" int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes,

@@ -17,7 +17,7 @@ namespace {
 
 constexpr int64_t kNoAllocMaxParticles = int64_t(1) << 20;  // 1,048,576 particles
 constexpr int kNoAllocMaxGrid = 64;                         // keys of at most 18 bits
-constexpr size_t kNoAllocScratchBytes = size_t(22) << 20;   // 22 MiB
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // 32 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -49,9 +49,9 @@ extern "C" int soax_sort_by_cell_noalloc(soax_t h, int32_t grid, uint32_t* perm_
   if (h->n == 0) return soax_sort_by_cell(h, grid, nullptr, 0, stream);
   void* ws = nullptr;
   if (int r = noalloc_scratch(&ws)) return r;
-  // The radix sort clears its per-pass digit totals itself; every other part of the
-  // scratch is fully written before it is read, so nothing left from an earlier call
-  // is used.
+  // The sort clears what it counts into (the cell sort's counts and gate, the radix
+  // sort's per-pass digit totals) itself; every other part of the scratch is fully
+  // written before it is read, so nothing left from an earlier call is used.
   if (int r = soax_sort_by_cell(h, grid, ws, kNoAllocScratchBytes, stream)) return r;
   if (perm_out) {
     uint32_t* perm = nullptr;

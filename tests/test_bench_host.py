@@ -63,3 +63,12 @@ def test_e2e_floor():
     fast = dict(link, **{"both_GB/s": 200.0})
     assert bench.e2e_floor(u, k, t, b, fast) > bench.e2e_floor(u, k, t, b, link)
     assert bench.e2e_floor(u, k, t, b, link) < u / t
+
+
+def test_source_hash_ignores_comments_only():
+    a = "int f(int x) {  // the step\n  return x + 1; /* one */\n}\n# build flag\n"
+    b = "/* header */\nint f(int x) {\n  return x + 1;\n}\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)
+    assert "#include <x>" in bench.code_only("#include <x>\n// note\n")

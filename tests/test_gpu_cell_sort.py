@@ -1,0 +1,102 @@
+"""The cell counting sort (grids up to 64^3: counts, bucket scan, scatter of equal-key
+groups, per-key order of the groups by segment) and its gated fallback to the radix
+passes, bit-exact against the oracle's stable argsort: near-sorted keys (the bench's
+case: a sorted set stepped again), random keys, keys at the per-key capacity (2048
+particles, 256 groups), keys beyond it (one key holding most particles: the radix passes
+sort), tiny and ragged sizes, and the sorted keys written beside the permutation."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1710_03462_b300 as sx
+import soax_inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _sort_keys(keys, grid, with_keys=True):
+    """sort_by_keys / sort_perm of the given u32 keys on a set of that size."""
+    n = keys.size
+    p = sx.Particles([("pos", "f64", 3, "P")], n)
+    kt = torch.from_numpy(keys.view(np.int32).copy()).cuda()
+    if with_keys:
+        sk, perm = p.sort_by_keys(grid, kt)
+        out = _u32(sk), _u32(perm)
+    else:
+        _, perm = p.sort_perm(grid, kt)
+        out = None, _u32(perm)
+    sx.sync()
+    return out
+
+
+def _check(keys, grid, with_keys=True):
+    sk, perm = _sort_keys(keys, grid, with_keys)
+    ref, rsk = oracle.stable_argsort(keys)
+    assert np.array_equal(perm, ref)
+    if with_keys:
+        assert np.array_equal(sk, rsk)
+
+
+@pytest.mark.parametrize("n,grid", [(1, 32), (2, 1), (31, 7), (33, 32), (4097, 64), (100003, 32), (250001, 64)])
+def test_random_keys(n, grid):
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, grid ** 3, n, dtype=np.uint32)
+    _check(keys, grid)
+    _check(keys, grid, with_keys=False)
+
+
+def test_near_sorted_keys_after_steps():
+    """The bench's case: a set sorted by cell, stepped 10 times, keyed again in its
+    sorted order (most keys in runs, a tenth of them moved to neighbouring cells)."""
+    n, grid = 1 << 20, 32
+    d = soax_inputs.basic_set(n, 3)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    p.load(d)
+    p.sort_by_cell(grid)
+    keys = p.step_fused(sx.Flow(), 10, grid=grid)
+    k = _u32(keys).copy()
+    moved = np.count_nonzero(np.diff(k.astype(np.int64)) != 0)
+    assert moved > n // 100  # not trivially sorted
+    ws = p.sort_workspace(grid)
+    _, perm = p.sort_perm(grid, keys, ws)
+    sx.sync()
+    ref, _ = oracle.stable_argsort(k)
+    assert np.array_equal(_u32(perm), ref)
+
+
+def test_capacity_edges():
+    """A key with exactly 2048 particles in 64 groups (the counting path), a key with 2049
+    (the radix passes), and a key with 257 groups of one particle (the radix passes)."""
+    grid = 16
+    base = np.repeat(np.arange(grid ** 3, dtype=np.uint32), 3)
+    k1 = np.sort(np.concatenate([base, np.full(2048 - 3, 77, np.uint32)]), kind="stable")
+    _check(k1, grid)
+    k2 = np.sort(np.concatenate([base, np.full(2049 - 3, 77, np.uint32)]), kind="stable")
+    _check(k2, grid)
+    # 257 groups of key 5: one per 32-key segment, the rest of each segment other keys.
+    k3 = np.arange(grid ** 3, dtype=np.uint32) % 4000 + 10
+    k3 = np.resize(k3, 257 * 32).copy()
+    k3[::32] = 5
+    _check(k3, grid)
+
+
+def test_one_cell_holds_most_particles():
+    """Clustered input beyond the per-key capacity: the gate hands the sort to the radix
+    passes, which give the same permutation."""
+    rng = np.random.default_rng(9)
+    n, grid = 300001, 32
+    keys = rng.integers(0, grid ** 3, n, dtype=np.uint32)
+    keys[rng.random(n) < 0.5] = 12345
+    _check(keys, grid)
+
+
+def test_grid_beyond_the_counting_sort():
+    """Grids above 64^3 (more than 18 key bits) sort with the radix passes alone."""
+    rng = np.random.default_rng(4)
+    keys = rng.integers(0, 100 ** 3, 70001, dtype=np.uint32)
+    _check(keys, 100)
