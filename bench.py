@@ -35,6 +35,7 @@ no collective on the data path); time = max over ranks; value = all ranks' parti
 / that time.
 """
 import argparse
+import ctypes
 import hashlib
 import glob
 import json
@@ -75,7 +76,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="soax", choices=["soax", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="skip the secondary rows")
-    ap.add_argument("--only", choices=["euler", "euler_sweep", "adjoint", "batched", "aos", "fixed", "plain", "wide"],
+    ap.add_argument("--only", choices=["euler", "euler_sweep", "adjoint", "batched", "aos", "fixed", "plain", "wide",
+                                       "sort"],
                     help="run only this secondary row (profiling captures)")
     ap.add_argument("--n", type=int, default=None, help="particles (default: the row's workload)")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="pieces per soax_step_host call in the e2e loop")
@@ -968,6 +970,46 @@ def row_wide_n64M(sx, torch, dev, n=None, intervals=None):
     return out
 
 
+def row_sort(sx, torch, dev, name, n=None):
+    """The cell sort of a workload's near-sorted keys (its bench interval: a set sorted by
+    cell, stepped sort_every steps, keyed again in that order), timed as the library's
+    soax_sort_perm (the cell counting sort, with the radix passes gated behind it) and as
+    the plain LSD radix sort of the same keys (soax_radix_sort_pairs, 2 passes), which
+    must give the same permutation; algorithmic bytes: keys read twice and the
+    permutation written (12 B per particle) for the counting sort, 32 B for the radix."""
+    w = soax_inputs.WORKLOADS[name]
+    n = w["n"] if n is None else n
+    grid = w["grid"]
+    wide = name == "wide_n64M"
+    d = soax_inputs.wide_set(n, w["seed"]) if wide else soax_inputs.basic_set(n, w["seed"])
+    schema = sx.WIDE_SCHEMA if wide else sx.BASIC_SCHEMA
+    p = sx.Particles(schema, n, device=dev)
+    p.load(d)
+    del d
+    f = (sx.Flow(A=w["A"], B=w["B"], C=w["C"], tau=0.0, dt=w["dt"], tau_field="mass", tau_scale=w["tau_scale"],
+                 acc="acc") if wide else sx.Flow(A=w["A"], B=w["B"], C=w["C"], tau=w["tau"], dt=w["dt"]))
+    ws = p.sort_workspace(grid)
+    p.sort_by_cell(grid, ws)
+    keys = p.step_fused(f, w["sort_every"], grid=grid)
+    bits = int(grid ** 3 - 1).bit_length()
+    stream = torch.cuda.current_stream(dev)
+    t_cell = _events(torch, stream, lambda: p.sort_perm(grid, keys, ws), reps=10)
+    perm_cell = p.sort_results(grid, ws)[1].clone()
+    nb = ctypes.c_size_t()  # the radix sort's own workspace
+    sx._check(sx.lib().soax_radix_workspace_bytes(n, bits, ctypes.byref(nb)))
+    rws = torch.empty(max(nb.value, 16), dtype=torch.uint8, device=dev)
+    vo = torch.empty(n, dtype=torch.int32, device=dev)
+    t_radix = _events(torch, stream, lambda: sx.radix_sort_pairs(keys, None, bits, want_keys=False, ws=rws, out=vo),
+                      reps=10)
+    same = bool(torch.equal(perm_cell, vo))
+    out = {"workload": name, "n": n, "grid": grid, "key_bits": bits, "same_permutation": same,
+           "cell_sort_ms": t_cell * 1e3, "radix_sort_ms": t_radix * 1e3, "radix_over_cell": t_radix / t_cell,
+           "cell_roofline": hbm_roofline(12, n, t_cell, None), "radix_roofline": hbm_roofline(32, n, t_radix, None)}
+    del p, ws, keys, rws, vo
+    torch.cuda.empty_cache()
+    return out
+
+
 def row_fixed(sx, torch, dev, n, nsteps_list):
     """Per-step and per-launch costs of the fused step: the bench's gather step (through
     a near-identity permutation), the fused step with keys and the plain fused step, each
@@ -1004,8 +1046,10 @@ def secondary_rows(sx, torch, p, d, dev):
     rows["aos_soa_roundtrip"], rows["aos_step"] = row_aos(sx, torch, p, flow)
     rows["fwd_adjoint"] = row_adjoint(sx, torch, dev)
     rows["batched"] = row_batched(sx, torch, dev)
+    rows["sort_sorted_n16M"] = row_sort(sx, torch, dev, "sorted_n16M")
     rows["plain_n65536"] = row_plain_n65536(sx, torch, dev)
     rows["wide_n64M"] = row_wide_n64M(sx, torch, dev)
+    rows["sort_wide_n64M"] = row_sort(sx, torch, dev, "wide_n64M")
     return rows
 
 
@@ -1022,6 +1066,9 @@ def run_only(args):
         row = row_adjoint(sx, torch, dev, args.n)
     elif args.only == "batched":
         row = row_batched(sx, torch, dev, args.nens, args.fixed_tune)
+    elif args.only == "sort":
+        row = {"sorted_n16M": row_sort(sx, torch, dev, "sorted_n16M", args.n),
+               "wide_n64M": row_sort(sx, torch, dev, "wide_n64M", args.n)}
     elif args.only == "plain":
         row = row_plain_n65536(sx, torch, dev)
     elif args.only == "wide":

@@ -554,9 +554,10 @@ class Particles:
         return loss, xb
 
 
-def radix_sort_pairs(keys, vals=None, key_bits=32, want_keys=True, ws=None, stream=None):
+def radix_sort_pairs(keys, vals=None, key_bits=32, want_keys=True, ws=None, stream=None, out=None):
     """Stable LSD radix sort of (u32 key, u32 value); vals None = argsort.  Tensors are
-    int32 holding the u32 bit patterns.  Returns (sorted keys or None, sorted values)."""
+    int32 holding the u32 bit patterns.  Returns (sorted keys or None, sorted values);
+    out: a tensor of n int32 to receive the sorted values (else one is allocated)."""
     n = keys.numel()
     b = C.c_size_t()
     _check(lib().soax_radix_workspace_bytes(n, int(key_bits), C.byref(b)))
@@ -564,8 +565,8 @@ def radix_sort_pairs(keys, vals=None, key_bits=32, want_keys=True, ws=None, stre
         ws = torch.empty(max(b.value, 16), dtype=torch.uint8, device=keys.device)
         _hold(stream, ws)
     ko = torch.empty_like(keys) if want_keys else None
-    vo = torch.empty(n, dtype=torch.int32, device=keys.device)
-    _hold(stream, ko, vo)
+    vo = torch.empty(n, dtype=torch.int32, device=keys.device) if out is None else out
+    _hold(stream, ko, vo if out is None else None)
     _check(lib().soax_radix_sort_pairs(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), n, int(key_bits), _ptr(ws),
                                        ws.numel(), _stream(stream)), "soax_radix_sort_pairs")
     return ko, vo

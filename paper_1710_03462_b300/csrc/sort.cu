@@ -133,29 +133,33 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_upsweep(const uint32_t* __
   if (gate && *gate == 0) return;
   __shared__ uint32_t hist[kMaxRadix];
   const int radix = (int)mask + 1, tid = threadIdx.x, lane = tid & 31;
-  for (int d = tid; d < radix; d += kSortBlock) hist[d] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kTile;
   const uint32_t lt = (1u << lane) - 1;
-  // All loads first, so that their latencies overlap.
-  uint32_t dg[kSortItems];
+  // One tile per block, or several when the grid is smaller than the tile count.
+  for (int64_t tile = blockIdx.x; tile < nblocks; tile += gridDim.x) {
+    for (int d = tid; d < radix; d += kSortBlock) hist[d] = 0;
+    __syncthreads();
+    const int64_t base = tile * kTile;
+    // All loads first, so that their latencies overlap.
+    uint32_t dg[kSortItems];
 #pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    const int64_t i = base + (int64_t)j * kSortBlock + tid;
-    dg[j] = i < n ? ((keys[i] >> shift) & mask) : 0xFFFFFFFFu;
-  }
+    for (int j = 0; j < kSortItems; ++j) {
+      const int64_t i = base + (int64_t)j * kSortBlock + tid;
+      dg[j] = i < n ? ((keys[i] >> shift) & mask) : 0xFFFFFFFFu;
+    }
 #pragma unroll
-  for (int j = 0; j < kSortItems; ++j) {
-    // Warp-aggregated increment: sorted input puts many equal digits in one warp.
-    const uint32_t d = dg[j];
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-    if (d != 0xFFFFFFFFu && (peers & lt) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
-  }
-  __syncthreads();
-  for (int d = tid; d < radix; d += kSortBlock) {
-    uint32_t c = hist[d];
-    counts[(int64_t)d * nblocks + blockIdx.x] = c;
-    if (c) atomicAdd(&totals[d], c);
+    for (int j = 0; j < kSortItems; ++j) {
+      // Warp-aggregated increment: sorted input puts many equal digits in one warp.
+      const uint32_t d = dg[j];
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+      if (d != 0xFFFFFFFFu && (peers & lt) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = tid; d < radix; d += kSortBlock) {
+      uint32_t c = hist[d];
+      counts[(int64_t)d * nblocks + tile] = c;
+      if (c) atomicAdd(&totals[d], c);
+    }
+    __syncthreads();
   }
 }
 
@@ -184,6 +188,9 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scan_rows(uint32_t* __re
   }
 }
 
+// LOOP: the grid may be smaller than the tile count (each block loops over tiles); without
+// it every block takes exactly its own tile.
+template <bool LOOP>
 __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n, int shift, uint32_t mask, int64_t nblocks,
@@ -198,9 +205,12 @@ __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
   uint32_t* sv = sk + kTile;                 // [tile] staged values
   __shared__ uint32_t scratch[33];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  bool over = false;
+  // One tile per block, or several when the grid is smaller than the tile count.
+  for (int64_t tile = blockIdx.x; tile < nblocks; tile += gridDim.x) {
   for (int k = tid; k < kSortWarps * radix; k += kSortBlock) wc[k] = 0;
   __syncthreads();
-  const int64_t tile0 = (int64_t)blockIdx.x * kTile;
+  const int64_t tile0 = tile * kTile;
   const int tcount = (int)(n - tile0 < kTile ? n - tile0 : kTile);
   const uint32_t lt = (1u << lane) - 1;
   uint32_t kr[kSortItems], vr[kSortItems], rk[kSortItems];
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
     if (d1 < radix) boff[d1] = ex + c0;
   }
   __syncthreads();
-  for (int d = tid; d < radix; d += kSortBlock) gbase[d] = counts[(int64_t)d * nblocks + blockIdx.x] - boff[d];
+  for (int d = tid; d < radix; d += kSortBlock) gbase[d] = counts[(int64_t)d * nblocks + tile] - boff[d];
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int li = w * (kTile / kSortWarps) + r * 32 + lane;
@@ -261,7 +271,6 @@ __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
     }
   }
   __syncthreads();
-  bool over = false;
   for (int li = tid; li < tcount; li += kSortBlock) {
     uint32_t key = sk[li];
     // Only a corrupted workspace (digit offsets overwritten meanwhile) puts dest outside
@@ -272,6 +281,9 @@ __global__ void __launch_bounds__(kSortBlock, 3) k_radix_downsweep(
     const uint32_t dest = min(raw, (uint32_t)n - 1u);
     if (keys_out) keys_out[dest] = key;
     vals_out[dest] = sv[li];
+  }
+  if constexpr (!LOOP) break;
+  __syncthreads();  // the tile's staging area and counters are free for the next tile
   }
   if (over) atomicExch(status, (int)SOAX_EINVAL);
 }
@@ -345,22 +357,25 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArg
 // the keys plus per-cell work, for keys that come in near cell order (the keys of the
 // particles a previous sort left in cell order, after a few steps).  Every aligned
 // 32-key segment of the input is cut into groups of equal keys (one warp match):
-//   count:   per key d, its particle count m_d and its number of groups C_d;
-//   scan:    bucket starts (exclusive sums of m) and group-record starts (of C);
+//   count:   per key d, its particle count m_d (one atomic per group), then the totals
+//            of every 4096 keys;
+//   scan:    bucket starts (exclusive sums of m);
 //   scatter: each group reserves cnt consecutive slots of its key's bucket (one atomic)
-//            and writes its indices there in lane order, and a record (segment, first
-//            slot, cnt) into its key's record range;
-//   order:   one warp per key: the bucket's groups come from distinct segments, i.e.
-//            disjoint ascending index ranges, so the stable order of the bucket is its
-//            groups ranked by segment; each group's destination is the count of the
-//            bucket's particles in groups of smaller segment, and one pass moves every
+//            and writes its indices there in lane order;
+//   order:   one warp per key: every group of the bucket is one chunk of consecutive
+//            slots, and chunks from different groups come from different segments
+//            (disjoint, ascending index ranges), so a chunk ends where the segment of
+//            the index (index / 32) changes, and the stable order of the bucket is its
+//            chunks ranked by segment; each chunk's destination is the count of the
+//            bucket's particles in chunks of smaller segment, and one pass moves every
 //            index there.
-// A key with more than kCellMaxParticles particles or kCellMaxGroups groups does not fit
-// the order kernel's per-warp buffers: the scan then raises the gate and the radix passes
-// (launched after, gated) sort instead; scatter and order return at once.  Nothing waits
-// on another block.
-constexpr int kCellMaxParticles = 2048;  // per key, for the per-warp shift table (int16)
-constexpr int kCellMaxGroups = 256;      // per key: 8 group records per lane
+// A key with more than kCellMaxParticles particles (found by the scan) or more than
+// kCellMaxGroups chunks (found by the order kernel) does not fit the per-warp buffers:
+// the gate is raised and the radix passes (launched after, gated) sort instead of this
+// sort; scatter and order return at once once it is raised.  Nothing waits on another
+// block.
+constexpr int kCellMaxParticles = 2048;  // per key: the per-warp chunk-id table
+constexpr int kCellMaxGroups = 256;      // per key: 8 chunk keys per lane in the warp sort
 constexpr int kCellChunk = 4096;         // keys per scan block
 constexpr int kCellBlock = 256;
 constexpr int kCellOrderWarps = 8;
@@ -371,92 +386,85 @@ struct CellSortArgs {
   uint32_t mask;           // 2^bits - 1; keys are taken modulo 2^bits, as the radix sort does
   int nb;                  // 2^bits buckets
   uint32_t* cnt;           // [nb] particle counts, then the slot cursors
-  uint32_t* grp;           // [nb] group counts, then the record cursors
   uint32_t* start;         // [nb + 1] bucket starts
-  uint32_t* gstart;        // [nb + 1] record starts
-  uint32_t* chunk_tot;     // [2 * nchunks] particle and group totals of each 4096-key chunk
+  uint32_t* chunk_tot;     // [nchunks] particle totals of each 4096 keys
   int* gate;               // 0: this sort's result stands; 1: the radix passes sort
   uint32_t* tmp;           // [n] indices in bucket order, unordered within a bucket
-  unsigned long long* rec; // [n] group records
   uint32_t* perm;          // [n] the stable argsort
   uint32_t* skeys;         // [n] sorted keys, or NULL
-  int* status;             // device status word: a record that points outside its bucket
 };
 
-__device__ __forceinline__ unsigned long long cell_rec(uint64_t seg, uint32_t slot, uint32_t cnt) {
-  return (seg << 36) | ((uint64_t)slot << 5) | (uint64_t)(cnt - 1);
-}
+// Segments per warp iteration in the count and scatter kernels: their key loads are in
+// flight together.
+constexpr int kSegBatch = 8;
 
 __global__ void __launch_bounds__(kCellBlock) k_cell_count(const __grid_constant__ CellSortArgs a) {
-  extern __shared__ uint32_t s_tot[];  // [2 * nchunks]
-  const int nchunks = (a.nb + kCellChunk - 1) / kCellChunk;
-  for (int k = threadIdx.x; k < 2 * nchunks; k += blockDim.x) s_tot[k] = 0;
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1;
   const int64_t nseg = (a.n + 31) / 32;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sg = w0; sg < nseg; sg += wstride) {
-    const int64_t i = sg * 32 + lane;
-    const uint32_t d = i < a.n ? (a.keys[i] & a.mask) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-    if (d != 0xFFFFFFFFu && (peers & lt) == 0) {
-      const uint32_t c = (uint32_t)__popc(peers);
-      atomicAdd(&a.cnt[d], c);
-      atomicAdd(&a.grp[d], 1u);
-      atomicAdd(&s_tot[2 * (d / kCellChunk)], c);
-      atomicAdd(&s_tot[2 * (d / kCellChunk) + 1], 1u);
+  for (int64_t sg0 = w0 * kSegBatch; sg0 < nseg; sg0 += wstride * kSegBatch) {
+    uint32_t d[kSegBatch];
+#pragma unroll
+    for (int k = 0; k < kSegBatch; ++k) {
+      const int64_t i = (sg0 + k) * 32 + lane;
+      d[k] = i < a.n ? (a.keys[i] & a.mask) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int k = 0; k < kSegBatch; ++k) {
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d[k]);
+      if (d[k] != 0xFFFFFFFFu && (peers & lt) == 0) atomicAdd(&a.cnt[d[k]], (uint32_t)__popc(peers));
     }
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < 2 * nchunks; k += blockDim.x)
-    if (s_tot[k]) atomicAdd(&a.chunk_tot[k], s_tot[k]);
 }
 
-// One block of kScanThreads per 4096 keys: bucket and record starts, the cursors, and
-// the gate for keys beyond the order kernel's capacity.
+// One block of kScanThreads per 4096 keys: the particle total of its keys.
+__global__ void __launch_bounds__(kScanThreads) k_cell_chunk_totals(const __grid_constant__ CellSortArgs a) {
+  __shared__ uint32_t scratch[33];
+  const int b0 = blockIdx.x * kCellChunk + threadIdx.x * 4;
+  uint32_t sm = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (b0 + j < a.nb) sm += a.cnt[b0 + j];
+  uint32_t tm;
+  block_excl_scan(sm, scratch, &tm);
+  if (threadIdx.x == 0) a.chunk_tot[blockIdx.x] = tm;
+}
+
+// One block of kScanThreads per 4096 keys: bucket starts, the slot cursors, and the gate
+// for keys with more particles than the order kernel takes.
 __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const __grid_constant__ CellSortArgs a) {
   __shared__ uint32_t scratch[33];
-  __shared__ uint32_t s_base[2];
+  __shared__ uint32_t s_base;
   const int c = blockIdx.x, tid = threadIdx.x;
-  if (tid < 2) {
+  if (tid == 0) {
     uint32_t b = 0;
-    for (int k = 0; k < c; ++k) b += a.chunk_tot[2 * k + tid];
-    s_base[tid] = b;
+    for (int k = 0; k < c; ++k) b += a.chunk_tot[k];
+    s_base = b;
   }
   __syncthreads();
   const int b0 = c * kCellChunk + tid * 4;
-  uint32_t m[4], g[4], sm = 0, sg = 0;
+  uint32_t m[4], sm = 0;
   bool big = false;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int b = b0 + j;
-    m[j] = b < a.nb ? a.cnt[b] : 0u;
-    g[j] = b < a.nb ? a.grp[b] : 0u;
-    big |= m[j] > (uint32_t)kCellMaxParticles || g[j] > (uint32_t)kCellMaxGroups;
+    m[j] = b0 + j < a.nb ? a.cnt[b0 + j] : 0u;
+    big |= m[j] > (uint32_t)kCellMaxParticles;
     sm += m[j];
-    sg += g[j];
   }
-  uint32_t tm, tg;
-  uint32_t em = block_excl_scan(sm, scratch, &tm) + s_base[0];
-  uint32_t eg = block_excl_scan(sg, scratch, &tg) + s_base[1];
+  uint32_t tm;
+  uint32_t em = block_excl_scan(sm, scratch, &tm) + s_base;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int b = b0 + j;
     if (b < a.nb) {
       a.start[b] = em;
-      a.gstart[b] = eg;
       a.cnt[b] = em;  // the slot cursor
-      a.grp[b] = eg;  // the record cursor
     }
     em += m[j];
-    eg += g[j];
   }
-  if (c == gridDim.x - 1 && tid == blockDim.x - 1) {
-    a.start[a.nb] = em;
-    a.gstart[a.nb] = eg;
-  }
+  if (c == gridDim.x - 1 && tid == blockDim.x - 1) a.start[a.nb] = em;
   if (big) atomicExch(a.gate, 1);
 }
 
@@ -467,96 +475,249 @@ __global__ void __launch_bounds__(kCellBlock) k_cell_scatter(const __grid_consta
   const int64_t nseg = (a.n + 31) / 32;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sg = w0; sg < nseg; sg += wstride) {
-    const int64_t i = sg * 32 + lane;
-    const uint32_t d = i < a.n ? (a.keys[i] & a.mask) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-    const int leader = __ffs(peers) - 1;
-    uint32_t slot = 0;
-    if (d != 0xFFFFFFFFu && lane == leader) {
-      const uint32_t c = (uint32_t)__popc(peers);
-      slot = atomicAdd(&a.cnt[d], c);
-      const uint32_t r = atomicAdd(&a.grp[d], 1u);
-      a.rec[r] = cell_rec((uint64_t)sg, slot, c);
+  for (int64_t sg0 = w0 * kSegBatch; sg0 < nseg; sg0 += wstride * kSegBatch) {
+    uint32_t d[kSegBatch], peers[kSegBatch], slot[kSegBatch];
+#pragma unroll
+    for (int k = 0; k < kSegBatch; ++k) {
+      const int64_t i = (sg0 + k) * 32 + lane;
+      d[k] = i < a.n ? (a.keys[i] & a.mask) : 0xFFFFFFFFu;
     }
-    slot = __shfl_sync(0xFFFFFFFFu, slot, leader);
-    if (d != 0xFFFFFFFFu) a.tmp[slot + __popc(peers & lt)] = (uint32_t)i;
+    // Every group's reservation first (independent atomics, in flight together) ...
+#pragma unroll
+    for (int k = 0; k < kSegBatch; ++k) {
+      peers[k] = __match_any_sync(0xFFFFFFFFu, d[k]);
+      slot[k] = 0;
+      if (d[k] != 0xFFFFFFFFu && (peers[k] & lt) == 0) slot[k] = atomicAdd(&a.cnt[d[k]], (uint32_t)__popc(peers[k]));
+    }
+    // ... then the indices into their slots.
+#pragma unroll
+    for (int k = 0; k < kSegBatch; ++k) {
+      const uint32_t sl = __shfl_sync(0xFFFFFFFFu, slot[k], __ffs(peers[k]) - 1);
+      if (d[k] != 0xFFFFFFFFu) a.tmp[sl + __popc(peers[k] & lt)] = (uint32_t)((sg0 + k) * 32 + lane);
+    }
   }
 }
 
-// One warp per key (warps stride over the keys).  K: group records per lane (C <= 32 K).
-template <int K>
-__device__ __forceinline__ void cell_order_bucket(const CellSortArgs& a, uint32_t st, uint32_t m, uint32_t g0,
-                                                  uint32_t C, int16_t* shift) {
+// Ascending bitonic sort of 32 K values held K per lane (lane l holds positions
+// l K .. l K + K - 1).
+template <int K, typename T>
+__device__ __forceinline__ void warp_bitonic(T (&r)[K]) {
   const int lane = threadIdx.x & 31;
-  unsigned long long r[K];
-  uint32_t dest[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const uint32_t q = (uint32_t)k * 32 + lane;
-    r[k] = q < C ? a.rec[g0 + q] : ~0ull;
-    dest[k] = 0;
-  }
-  // dest = the particles in groups of smaller segment (segments are distinct per key).
+  for (int kk = 2; kk <= 32 * K; kk <<= 1) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    for (int sl = 0; sl < 32; ++sl) {
-      const unsigned long long o = __shfl_sync(0xFFFFFFFFu, r[k], sl);
-      const uint32_t oc = (uint32_t)(o & 31) + 1;
-      const bool valid = (uint32_t)k * 32 + sl < C;
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j < K) {  // both partners in this lane
 #pragma unroll
-      for (int j = 0; j < K; ++j)
-        if (valid && (o >> 36) < (r[j] >> 36)) dest[j] += oc;
+        for (int k = 0; k < K; ++k) {
+          const int p = k ^ j;
+          if (p > k) {
+            const bool up = ((lane * K + k) & kk) == 0;
+            const T x = r[k], y = r[p];
+            const bool sw = up ? (x > y) : (x < y);
+            r[k] = sw ? y : x;
+            r[p] = sw ? x : y;
+          }
+        }
+      } else {  // the partner in lane ^ (j / K), same register
+        const int lj = j / K;
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const T o = __shfl_xor_sync(0xFFFFFFFFu, r[k], lj);
+          const bool up = ((lane * K + k) & kk) == 0;
+          r[k] = (lower == up) ? (r[k] < o ? r[k] : o) : (r[k] > o ? r[k] : o);
+        }
+      }
     }
   }
-  // Only a workspace overwritten while the sort runs can hold a record outside its
-  // bucket: such a record is skipped, a destination outside the bucket clamped, and
-  // SOAX_EINVAL recorded (a wrong order, no access out of bounds).
-  bool bad = false;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if ((uint32_t)k * 32 + lane < C) {
-      const uint32_t off = (uint32_t)((r[k] >> 5) & 0x7FFFFFFFu) - st;
-      const uint32_t cnt = (uint32_t)(r[k] & 31) + 1;
-      const int16_t sh = (int16_t)((int32_t)dest[k] - (int32_t)off);
-      if (off < m && cnt <= m - off)
-        for (uint32_t t = 0; t < cnt; ++t) shift[off + t] = sh;
-      else
-        bad = true;
-    }
-  }
-  __syncwarp();
-  for (uint32_t j = lane; j < m; j += 32) {
-    const int32_t q = (int32_t)j + shift[j];
-    bad |= q < 0 || q >= (int32_t)m;
-    a.perm[st + (uint32_t)min(max(q, 0), (int32_t)m - 1)] = a.tmp[st + j];
-  }
-  if (bad) atomicExch(a.status, (int)SOAX_EINVAL);
-  __syncwarp();
 }
 
-__global__ void __launch_bounds__(kCellOrderWarps * 32) k_cell_order(const __grid_constant__ CellSortArgs a) {
-  if (*a.gate) return;
-  __shared__ int16_t s_shift[kCellOrderWarps][kCellMaxParticles];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t wstride = (int64_t)gridDim.x * kCellOrderWarps;
-  for (int64_t d = (int64_t)blockIdx.x * kCellOrderWarps + w; d < a.nb; d += wstride) {
-    const uint32_t st = a.start[d], m = a.start[d + 1] - st;
-    if (m == 0) continue;
-    if (a.skeys)
-      for (uint32_t j = lane; j < m; j += 32) a.skeys[st + j] = (uint32_t)d;
-    const uint32_t g0 = a.gstart[d], C = a.gstart[d + 1] - g0;
-    if (C == 1) {  // one group: already in order
-      for (uint32_t j = lane; j < m; j += 32) a.perm[st + j] = a.tmp[st + j];
-    } else if (C <= 32) {
-      cell_order_bucket<1>(a, st, m, g0, C, s_shift[w]);
-    } else if (C <= 64) {
-      cell_order_bucket<2>(a, st, m, g0, C, s_shift[w]);
-    } else if (C <= 128) {
-      cell_order_bucket<4>(a, st, m, g0, C, s_shift[w]);
-    } else {
-      cell_order_bucket<8>(a, st, m, g0, C, s_shift[w]);
+// Per-warp tables of the order kernel.
+struct CellWarpSmem {
+  uint16_t cid[kCellMaxParticles];   // chunk of each slot
+  uint16_t coff[kCellMaxGroups + 1]; // first slot of each chunk (coff[C] = m)
+  uint16_t cdst[kCellMaxGroups];     // destination of each chunk's first slot
+  uint32_t cseg[kCellMaxGroups];     // segment of each chunk
+};
+
+// The chunks of a bucket ranked by segment (C <= 32 K): their destinations into t.cdst.
+// The sort key is (segment, chunk): 32 bits while every segment is below 2^24 - 1
+// (fewer than 2^29 - 32 particles), else 64; padding is all ones, above every key.
+template <int K, typename T>
+__device__ __forceinline__ void cell_rank_chunks(CellWarpSmem& t, uint32_t C) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kShift = sizeof(T) == 4 ? 8 : 16;
+  constexpr T kNone = ~T(0);
+  T r[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t c = (uint32_t)(lane * K + k);
+    r[k] = c < C ? (T)(((T)t.cseg[c] << kShift) | c) : kNone;
+  }
+  warp_bitonic<K, T>(r);
+  uint32_t cn[K], cc[K], local = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    cc[k] = (uint32_t)(r[k] & ((T(1) << kShift) - 1));
+    cn[k] = r[k] == kNone ? 0u : (uint32_t)t.coff[cc[k] + 1] - t.coff[cc[k]];
+    local += cn[k];
+  }
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  uint32_t dest = incl - local;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (cn[k]) t.cdst[cc[k]] = (uint16_t)dest;
+    dest += cn[k];
+  }
+}
+
+// Chunk discovery over R rows of 32 slots (v: the indices, rows r0 ..): a slot starts a
+// chunk where its index's segment differs from the previous slot's.  C and carry (the
+// previous row's last segment) run across calls.
+template <int R>
+__device__ __forceinline__ void cell_find_chunks(const uint32_t (&v)[R], uint32_t r0, uint32_t m, uint32_t& C,
+                                                 uint32_t& carry, CellWarpSmem& t) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1;
+#pragma unroll
+  for (int b = 0; b < R; ++b) {
+    const uint32_t j = (r0 + b) * 32 + lane;
+    const uint32_t sg = j < m ? (v[b] >> 5) : 0xFFFFFFFFu;
+    uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, sg, 1);
+    if (lane == 0) prev = carry;
+    const bool s0 = j < m && sg != prev;
+    const uint32_t mk = __ballot_sync(0xFFFFFFFFu, s0);
+    const uint32_t c = C + __popc(mk & lt) - (s0 ? 0u : 1u);  // this slot's chunk
+    if (j < m && c < (uint32_t)kCellMaxGroups) {
+      t.cid[j] = (uint16_t)c;
+      if (s0) {
+        t.coff[c] = (uint16_t)j;
+        t.cseg[c] = sg;
+      }
     }
+    C += __popc(mk);
+    carry = __shfl_sync(0xFFFFFFFFu, sg, 31);
+  }
+}
+
+// Every slot of R rows (v: the indices) to its chunk's destination.
+template <int R>
+__device__ __forceinline__ void cell_move(const uint32_t (&v)[R], uint32_t r0, uint32_t m, const CellWarpSmem& t,
+                                          uint32_t* perm) {
+  const int lane = threadIdx.x & 31;
+  uint32_t q[R];
+#pragma unroll
+  for (int b = 0; b < R; ++b) {
+    const uint32_t j = (r0 + b) * 32 + lane;
+    if (j < m) {
+      const uint32_t c = t.cid[j];
+      q[b] = (uint32_t)t.cdst[c] + (j - t.coff[c]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < R; ++b) {
+    const uint32_t j = (r0 + b) * 32 + lane;
+    if (j < m) perm[q[b]] = v[b];
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void cell_load_rows(const uint32_t* src, uint32_t r0, uint32_t m, uint32_t (&v)[R]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int b = 0; b < R; ++b) {
+    const uint32_t j = (r0 + b) * 32 + lane;
+    v[b] = j < m ? src[j] : 0u;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void cell_rank_t(CellWarpSmem& t, uint32_t C) {
+  if (C <= 32)
+    cell_rank_chunks<1, T>(t, C);
+  else if (C <= 64)
+    cell_rank_chunks<2, T>(t, C);
+  else if (C <= 128)
+    cell_rank_chunks<4, T>(t, C);
+  else
+    cell_rank_chunks<8, T>(t, C);
+}
+
+constexpr int kOrderRowsHeld = 16;  // a bucket of up to 512 slots stays in registers
+constexpr int kOrderRows = 8;       // larger buckets: rows of 32 slots loaded together
+
+template <typename T>
+__global__ void __launch_bounds__(kCellOrderWarps * 32, 3) k_cell_order(const __grid_constant__ CellSortArgs a) {
+  if (*a.gate) return;
+  __shared__ CellWarpSmem s_tab[kCellOrderWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  CellWarpSmem& t = s_tab[w];
+  const int64_t wstride = (int64_t)gridDim.x * kCellOrderWarps;
+  int64_t d = (int64_t)blockIdx.x * kCellOrderWarps + w;
+  uint32_t st = 0, en = 0;
+  if (d < a.nb) {
+    st = a.start[d];
+    en = a.start[d + 1];
+  }
+  for (; d < a.nb; d += wstride) {
+    // The next bucket's bounds, read while this one is ordered.
+    const int64_t dn = d + wstride;
+    uint32_t stn = 0, enn = 0;
+    if (dn < a.nb) {
+      stn = a.start[dn];
+      enn = a.start[dn + 1];
+    }
+    const uint32_t m = en - st;
+    if (m > 0) {
+      if (a.skeys)
+        for (uint32_t j = lane; j < m; j += 32) a.skeys[st + j] = (uint32_t)d;
+      uint32_t C = 0, carry = 0xFFFFFFFFu;
+      bool over = false;
+      if (m <= 32 * kOrderRowsHeld) {
+        uint32_t v[kOrderRowsHeld];
+        cell_load_rows<kOrderRowsHeld>(a.tmp + st, 0, m, v);
+        cell_find_chunks<kOrderRowsHeld>(v, 0, m, C, carry, t);
+        over = C > (uint32_t)kCellMaxGroups;
+        if (!over) {
+          if (lane == 0) t.coff[C] = (uint16_t)m;
+          __syncwarp();
+          cell_rank_t<T>(t, C);
+          __syncwarp();
+          cell_move<kOrderRowsHeld>(v, 0, m, t, a.perm + st);
+        }
+      } else {
+        for (uint32_t r0 = 0; r0 * 32 < m; r0 += kOrderRows) {
+          uint32_t v[kOrderRows];
+          cell_load_rows<kOrderRows>(a.tmp + st, r0, m, v);
+          cell_find_chunks<kOrderRows>(v, r0, m, C, carry, t);
+        }
+        over = C > (uint32_t)kCellMaxGroups;
+        if (!over) {
+          if (lane == 0) t.coff[C] = (uint16_t)m;
+          __syncwarp();
+          cell_rank_t<T>(t, C);
+          __syncwarp();
+          for (uint32_t r0 = 0; r0 * 32 < m; r0 += kOrderRows) {
+            uint32_t v[kOrderRows];
+            cell_load_rows<kOrderRows>(a.tmp + st, r0, m, v);
+            cell_move<kOrderRows>(v, r0, m, t, a.perm + st);
+          }
+        }
+      }
+      if (over) {  // beyond the warp's tables: the radix passes sort
+        if (lane == 0) atomicExch(a.gate, 1);
+        return;
+      }
+      __syncwarp();
+    }
+    st = stn;
+    en = enn;
   }
 }
 
@@ -571,11 +732,11 @@ struct SortWs {
   size_t off_keys, off_skeys, off_perm, off_radix, total;
   RadixPlan rp;
   // The cell counting sort (grids up to 64^3): its zeroed header (gate, counts, chunk
-  // totals), bucket and record starts, and its index and record arrays, which share the
-  // radix region (the radix passes only run, gated, after the counting sort is done).
+  // totals), the bucket starts, and its index array, which shares the radix region (the
+  // radix passes only run, gated, after the counting sort is done).
   bool cell = false;
   int bits = 0, nb = 0, nchunks = 0;
-  size_t off_hdr = 0, hdr_bytes = 0, off_start = 0, off_gstart = 0, off_tmp = 0, off_rec = 0;
+  size_t off_hdr = 0, hdr_bytes = 0, off_start = 0, off_tmp = 0;
 };
 
 constexpr int kCellMaxBits = 18;
@@ -595,21 +756,17 @@ static SortWs sort_ws_plan(int64_t n, int G) {
   if (w.cell) {
     w.nb = 1 << w.bits;
     w.nchunks = (w.nb + kCellChunk - 1) / kCellChunk;
-    w.off_hdr = off;  // gate (256 B), cnt[nb], grp[nb], chunk totals[2 nchunks]
-    w.hdr_bytes = 256 + (size_t)w.nb * 8 + (size_t)w.nchunks * 8;
+    w.off_hdr = off;  // gate (256 B), cnt[nb], chunk totals[nchunks]
+    w.hdr_bytes = 256 + (size_t)w.nb * 4 + (size_t)w.nchunks * 4;
     off = align256(off + w.hdr_bytes);
     w.off_start = off;
-    off = align256(off + (size_t)(w.nb + 1) * 4);
-    w.off_gstart = off;
     off = align256(off + (size_t)(w.nb + 1) * 4);
   }
   w.off_radix = off;
   size_t tail = w.rp.total;
   if (w.cell) {
     w.off_tmp = off;
-    w.off_rec = align256(off + (size_t)n * 4);
-    const size_t cell_tail = w.off_rec + (size_t)n * 8 - off;
-    if (cell_tail > tail) tail = cell_tail;
+    if ((size_t)n * 4 > tail) tail = (size_t)n * 4;
   }
   w.total = off + tail;
   return w;
@@ -679,13 +836,15 @@ static int radix_sort_gated(const uint32_t* keys_in, const uint32_t* vals_in, ui
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)downsweep_smem(kMaxRadix));
-    // Prefer shared memory over L1 so that three 53 KB blocks fit on an SM.
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_radix_downsweep, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: smem attribute");
+    for (const void* fn : {(const void*)k_radix_downsweep<false>, (const void*)k_radix_downsweep<true>}) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)downsweep_smem(kMaxRadix));
+      // Prefer shared memory over L1 so that three 53 KB blocks fit on an SM.
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: smem attribute");
+    }
     attr_set[dev] = true;
   }
   char* w = static_cast<char*>(ws);
@@ -708,13 +867,23 @@ static int radix_sort_gated(const uint32_t* keys_in, const uint32_t* vals_in, ui
     uint32_t* vout = last ? vals_out : av[pass & 1];
     cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)radix * 4, s);
     if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: memset");
-    k_radix_upsweep<<<(unsigned)p.nblocks, kSortBlock, 0, s>>>(kin, n, shift, mask, p.nblocks, counts, totals, gate);
+    // Gated (behind the cell counting sort, usually with nothing to do): grids that fill
+    // the GPU once, each block looping over tiles, so that returning at once costs little.
+    const unsigned gu = gate ? (unsigned)persistent_grid((const void*)k_radix_upsweep, kSortBlock, 0, p.nblocks)
+                             : (unsigned)p.nblocks;
+    const unsigned gd = gate ? (unsigned)persistent_grid((const void*)k_radix_downsweep<true>, kSortBlock,
+                                                         downsweep_smem(radix), p.nblocks)
+                             : (unsigned)p.nblocks;
+    k_radix_upsweep<<<gu, kSortBlock, 0, s>>>(kin, n, shift, mask, p.nblocks, counts, totals, gate);
     if (int r = check_launch("radix upsweep")) return r;
     k_radix_scan_rows<<<radix, kScanThreads, 0, s>>>(counts, totals, p.nblocks, gate);
     if (int r = check_launch("radix scan")) return r;
-    k_radix_downsweep<<<(unsigned)p.nblocks, kSortBlock, downsweep_smem(radix), s>>>(kin, vin, kout, vout, n, shift,
-                                                                                    mask, p.nblocks, counts, status,
-                                                                                    gate);
+    if (gate)
+      k_radix_downsweep<true><<<gd, kSortBlock, downsweep_smem(radix), s>>>(kin, vin, kout, vout, n, shift, mask,
+                                                                           p.nblocks, counts, status, gate);
+    else
+      k_radix_downsweep<false><<<gd, kSortBlock, downsweep_smem(radix), s>>>(kin, vin, kout, vout, n, shift, mask,
+                                                                            p.nblocks, counts, status, gate);
     if (int r = check_launch("radix downsweep")) return r;
   }
   return SOAX_OK;
@@ -813,32 +982,34 @@ static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, i
   a.nb = w.nb;
   a.gate = reinterpret_cast<int*>(base + w.off_hdr);
   a.cnt = reinterpret_cast<uint32_t*>(base + w.off_hdr + 256);
-  a.grp = a.cnt + w.nb;
-  a.chunk_tot = a.grp + w.nb;
+  a.chunk_tot = a.cnt + w.nb;
   a.start = reinterpret_cast<uint32_t*>(base + w.off_start);
-  a.gstart = reinterpret_cast<uint32_t*>(base + w.off_gstart);
   a.tmp = reinterpret_cast<uint32_t*>(base + w.off_tmp);
-  a.rec = reinterpret_cast<unsigned long long*>(base + w.off_rec);
   a.perm = perm;
   a.skeys = skeys;
-  a.status = status_word();
-  if (!a.status) return fail(SOAX_ECUDA, "cell sort: status word");
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaMemsetAsync(base + w.off_hdr, 0, w.hdr_bytes, s);
   if (e != cudaSuccess) return cuda_fail(e, "cell sort: memset");
-  const int64_t seg_blocks = ((n + 31) / 32 + kCellBlock / 32 - 1) / (kCellBlock / 32);
-  const size_t count_smem = (size_t)w.nchunks * 8;
-  const int gc = persistent_grid((const void*)k_cell_count, kCellBlock, count_smem, seg_blocks);
-  k_cell_count<<<gc, kCellBlock, count_smem, s>>>(a);
+  const int64_t seg_blocks = ((n + 31) / 32 + kSegBatch * (kCellBlock / 32) - 1) / (kSegBatch * (kCellBlock / 32));
+  const int gc = persistent_grid((const void*)k_cell_count, kCellBlock, 0, seg_blocks);
+  k_cell_count<<<gc, kCellBlock, 0, s>>>(a);
   if (int r = check_launch("cell sort: count")) return r;
+  k_cell_chunk_totals<<<w.nchunks, kScanThreads, 0, s>>>(a);
+  if (int r = check_launch("cell sort: chunk totals")) return r;
   k_cell_scan<<<w.nchunks, kScanThreads, 0, s>>>(a);
   if (int r = check_launch("cell sort: scan")) return r;
   const int gs = persistent_grid((const void*)k_cell_scatter, kCellBlock, 0, seg_blocks);
   k_cell_scatter<<<gs, kCellBlock, 0, s>>>(a);
   if (int r = check_launch("cell sort: scatter")) return r;
-  const int go = persistent_grid((const void*)k_cell_order, kCellOrderWarps * 32, 0,
-                                 (w.nb + kCellOrderWarps - 1) / kCellOrderWarps);
-  k_cell_order<<<go, kCellOrderWarps * 32, 0, s>>>(a);
+  // Chunk sort keys of 32 bits while every segment (index / 32) is below 2^24 - 1 (so no
+  // key reaches the all-ones padding value).
+  const bool narrow = n <= (int64_t(1) << 29) - 64;
+  const void* ko = narrow ? (const void*)k_cell_order<uint32_t> : (const void*)k_cell_order<unsigned long long>;
+  const int go = persistent_grid(ko, kCellOrderWarps * 32, 0, (w.nb + kCellOrderWarps - 1) / kCellOrderWarps);
+  if (narrow)
+    k_cell_order<uint32_t><<<go, kCellOrderWarps * 32, 0, s>>>(a);
+  else
+    k_cell_order<unsigned long long><<<go, kCellOrderWarps * 32, 0, s>>>(a);
   if (int r = check_launch("cell sort: order")) return r;
   return radix_sort_gated(keys, nullptr, skeys, perm, n, w.bits, base + w.off_radix, w.rp.total, stream, a.gate);
 }
