@@ -474,7 +474,7 @@ def run_soax(args):
     # at this speed against the copy peak, and the FP32 work against the FP32 pipes.
     roofline["hbm_equivalent"] = hbm_equivalent(BYTES_PER_PARTICLE_STEP, n * RK2_PER_STEP, fused_s)
     roofline["fp32"] = fp32_fraction(torch, dev, STEP_KERNEL, n * RK2_PER_STEP, fused_s)
-    sort_launches = 3 * 2  # (upsweep, scan, downsweep) x 2 passes; keys and permute-gather ride on the step
+    sort_launches = sort_kernel_launches(WL["grid"])  # keys and permute-gather ride on the step
     line = {
         "metric": METRIC, "value": tot_units / max_el, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_el / args.steps * 1e3,
@@ -505,6 +505,16 @@ def run_soax(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def sort_kernel_launches(grid):
+    """Kernels one soax_sort_perm launches on a grid^3 grid: the cell counting sort's six
+    (probe, count, chunk totals, scan, scatter, order) for up to 18 key bits, then the
+    radix passes' three each (upsweep, scan, downsweep; gated behind the counting sort,
+    they launch and return at once unless it could not take the keys)."""
+    bits = max(1, int(grid ** 3 - 1).bit_length())
+    passes = (bits + 8) // 9
+    return (6 if bits <= 18 else 0) + 3 * passes
 
 
 def e2e_floor(units_per_step, steps, gap_seconds, state_bytes, link):

@@ -357,6 +357,8 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArg
 // the keys plus per-cell work, for keys that come in near cell order (the keys of the
 // particles a previous sort left in cell order, after a few steps).  Every aligned
 // 32-key segment of the input is cut into groups of equal keys (one warp match):
+//   probe:   groups per segment on sample segments: keys in no particular order leave
+//            the sort to the radix passes at once (below);
 //   count:   per key d, its particle count m_d (one atomic per group), then the totals
 //            of every 4096 keys;
 //   scan:    bucket starts (exclusive sums of m);
@@ -389,6 +391,7 @@ struct CellSortArgs {
   uint32_t* start;         // [nb + 1] bucket starts
   uint32_t* chunk_tot;     // [nchunks] particle totals of each 4096 keys
   int* gate;               // 0: this sort's result stands; 1: the radix passes sort
+  uint32_t* probe;         // [2] sampled segments and their groups
   uint32_t* tmp;           // [n] indices in bucket order, unordered within a bucket
   uint32_t* perm;          // [n] the stable argsort
   uint32_t* skeys;         // [n] sorted keys, or NULL
@@ -398,7 +401,39 @@ struct CellSortArgs {
 // flight together.
 constexpr int kSegBatch = 8;
 
+// The probe: groups per segment on evenly spread sample segments (one per warp of the
+// launch).  Keys in no particular order (a set never sorted) give up to 32 groups per
+// segment and would overflow the order kernel's chunk tables after a full count and
+// scatter; with more than kProbeGroups groups per segment on average the count raises the
+// gate first and the counting sort returns at once.
+constexpr int kProbeGroups = 12;
+constexpr int kProbeBlocks = 148;
+
+__global__ void __launch_bounds__(kCellBlock) k_cell_probe(const __grid_constant__ CellSortArgs a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1;
+  const int64_t nseg = (a.n + 31) / 32;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wid >= nseg) return;  // uniform per warp
+  const int64_t sg = nseg <= nw ? wid : wid * nseg / nw;
+  const int64_t i = sg * 32 + lane;
+  const uint32_t d = i < a.n ? (a.keys[i] & a.mask) : 0xFFFFFFFFu;
+  const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+  const uint32_t lead = __ballot_sync(0xFFFFFFFFu, d != 0xFFFFFFFFu && (peers & lt) == 0);
+  if (lane == 0) {
+    atomicAdd(&a.probe[0], 1u);
+    atomicAdd(&a.probe[1], (uint32_t)__popc(lead));
+  }
+}
+
 __global__ void __launch_bounds__(kCellBlock) k_cell_count(const __grid_constant__ CellSortArgs a) {
+  // Keys in no particular order: the radix passes sort (the probe's verdict, uniform).
+  if (a.probe[1] > (uint32_t)kProbeGroups * a.probe[0]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.gate, 1);
+    return;
+  }
+  if (*a.gate) return;
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1;
   const int64_t nseg = (a.n + 31) / 32;
@@ -421,6 +456,7 @@ __global__ void __launch_bounds__(kCellBlock) k_cell_count(const __grid_constant
 
 // One block of kScanThreads per 4096 keys: the particle total of its keys.
 __global__ void __launch_bounds__(kScanThreads) k_cell_chunk_totals(const __grid_constant__ CellSortArgs a) {
+  if (*a.gate) return;
   __shared__ uint32_t scratch[33];
   const int b0 = blockIdx.x * kCellChunk + threadIdx.x * 4;
   uint32_t sm = 0;
@@ -435,6 +471,7 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_chunk_totals(const __grid
 // One block of kScanThreads per 4096 keys: bucket starts, the slot cursors, and the gate
 // for keys with more particles than the order kernel takes.
 __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const __grid_constant__ CellSortArgs a) {
+  if (*a.gate) return;
   __shared__ uint32_t scratch[33];
   __shared__ uint32_t s_base;
   const int c = blockIdx.x, tid = threadIdx.x;
@@ -756,7 +793,7 @@ static SortWs sort_ws_plan(int64_t n, int G) {
   if (w.cell) {
     w.nb = 1 << w.bits;
     w.nchunks = (w.nb + kCellChunk - 1) / kCellChunk;
-    w.off_hdr = off;  // gate (256 B), cnt[nb], chunk totals[nchunks]
+    w.off_hdr = off;  // gate and probe counters (256 B), cnt[nb], chunk totals[nchunks]
     w.hdr_bytes = 256 + (size_t)w.nb * 4 + (size_t)w.nchunks * 4;
     off = align256(off + w.hdr_bytes);
     w.off_start = off;
@@ -981,6 +1018,7 @@ static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, i
   a.mask = (uint32_t)(w.nb - 1);
   a.nb = w.nb;
   a.gate = reinterpret_cast<int*>(base + w.off_hdr);
+  a.probe = reinterpret_cast<uint32_t*>(base + w.off_hdr + 16);
   a.cnt = reinterpret_cast<uint32_t*>(base + w.off_hdr + 256);
   a.chunk_tot = a.cnt + w.nb;
   a.start = reinterpret_cast<uint32_t*>(base + w.off_start);
@@ -991,6 +1029,8 @@ static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, i
   cudaError_t e = cudaMemsetAsync(base + w.off_hdr, 0, w.hdr_bytes, s);
   if (e != cudaSuccess) return cuda_fail(e, "cell sort: memset");
   const int64_t seg_blocks = ((n + 31) / 32 + kSegBatch * (kCellBlock / 32) - 1) / (kSegBatch * (kCellBlock / 32));
+  k_cell_probe<<<kProbeBlocks, kCellBlock, 0, s>>>(a);
+  if (int r = check_launch("cell sort: probe")) return r;
   const int gc = persistent_grid((const void*)k_cell_count, kCellBlock, 0, seg_blocks);
   k_cell_count<<<gc, kCellBlock, 0, s>>>(a);
   if (int r = check_launch("cell sort: count")) return r;

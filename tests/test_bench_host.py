@@ -72,3 +72,9 @@ def test_source_hash_ignores_comments_only():
     assert bench.code_only(a) == bench.code_only(b)
     assert bench.code_only(a) != bench.code_only(c)
     assert "#include <x>" in bench.code_only("#include <x>\n// note\n")
+
+
+def test_sort_kernel_launches():
+    assert bench.sort_kernel_launches(32) == 6 + 6   # 15 bits: counting sort + 2 gated radix passes
+    assert bench.sort_kernel_launches(64) == 6 + 6   # 18 bits
+    assert bench.sort_kernel_launches(100) == 9      # 20 bits: the radix passes alone

@@ -100,3 +100,22 @@ def test_grid_beyond_the_counting_sort():
     rng = np.random.default_rng(4)
     keys = rng.integers(0, 100 ** 3, 70001, dtype=np.uint32)
     _check(keys, 100)
+
+
+def test_unordered_then_near_sorted_sets():
+    """A set in no particular order (the probe hands it to the radix passes) and then the
+    same set sorted and stepped (the counting sort): both give the oracle's permutation."""
+    n, grid = 400003, 32
+    d = soax_inputs.basic_set(n, 12)
+    p = sx.Particles(sx.BASIC_SCHEMA, n)
+    p.load(d)
+    ws = p.sort_workspace(grid)
+    keys = p.cell_keys(grid)
+    _, perm = p.sort_perm(grid, keys, ws)
+    sx.sync()
+    assert np.array_equal(_u32(perm), oracle.stable_argsort(_u32(keys).copy())[0])
+    p.sort_by_cell(grid, ws)
+    keys = p.step_fused(sx.Flow(), 10, grid=grid)
+    _, perm = p.sort_perm(grid, keys, ws)
+    sx.sync()
+    assert np.array_equal(_u32(perm), oracle.stable_argsort(_u32(keys).copy())[0])
