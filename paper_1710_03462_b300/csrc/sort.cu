@@ -526,11 +526,12 @@ __global__ void __launch_bounds__(kCellBlock) k_cell_scatter(const __grid_consta
       slot[k] = 0;
       if (d[k] != 0xFFFFFFFFu && (peers[k] & lt) == 0) slot[k] = atomicAdd(&a.cnt[d[k]], (uint32_t)__popc(peers[k]));
     }
-    // ... then the indices into their slots.
+    // ... then the indices into their slots (a slot beyond the n indices, only possible
+    // if the workspace is overwritten while the sort runs, is not written).
 #pragma unroll
     for (int k = 0; k < kSegBatch; ++k) {
-      const uint32_t sl = __shfl_sync(0xFFFFFFFFu, slot[k], __ffs(peers[k]) - 1);
-      if (d[k] != 0xFFFFFFFFu) a.tmp[sl + __popc(peers[k] & lt)] = (uint32_t)((sg0 + k) * 32 + lane);
+      const uint32_t sl = __shfl_sync(0xFFFFFFFFu, slot[k], __ffs(peers[k]) - 1) + __popc(peers[k] & lt);
+      if (d[k] != 0xFFFFFFFFu && sl < (uint32_t)a.n) a.tmp[sl] = (uint32_t)((sg0 + k) * 32 + lane);
     }
   }
 }
@@ -709,6 +710,12 @@ __global__ void __launch_bounds__(kCellOrderWarps * 32, 3) k_cell_order(const __
     if (dn < a.nb) {
       stn = a.start[dn];
       enn = a.start[dn + 1];
+    }
+    // Bounds outside the n slots (only possible if the workspace is overwritten while
+    // the sort runs): the radix passes sort instead (uniform per warp).
+    if (st > en || en > (uint32_t)a.n) {
+      if (lane == 0) atomicExch(a.gate, 1);
+      return;
     }
     const uint32_t m = en - st;
     if (m > 0) {
