@@ -508,13 +508,14 @@ def run_soax(args):
 
 
 def sort_kernel_launches(grid):
-    """Kernels one soax_sort_perm launches on a grid^3 grid: the cell counting sort's six
-    (probe, count, chunk totals, scan, scatter, order) for up to 18 key bits, then the
-    radix passes' three each (upsweep, scan, downsweep; gated behind the counting sort,
-    they launch and return at once unless it could not take the keys)."""
+    """Kernels one soax_sort_perm launches on a grid^3 grid: for up to 18 key bits the
+    cell counting sort's graph, six kernels (probe, count, chunk totals, scan, scatter,
+    order) and the one that opens its conditional node (the radix passes in its body run
+    only for keys the counting sort cannot take); beyond, the radix passes' three kernels
+    each (upsweep, scan, downsweep)."""
     bits = max(1, int(grid ** 3 - 1).bit_length())
     passes = (bits + 8) // 9
-    return (6 if bits <= 18 else 0) + 3 * passes
+    return 7 if bits <= 18 else 3 * passes
 
 
 def e2e_floor(units_per_step, steps, gap_seconds, state_bytes, link):

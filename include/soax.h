@@ -16,7 +16,9 @@
  *  - Ownership: the library owns only the host-side handle.  Particle planes, shadow
  *    planes, AoS buffers, keys, permutations and workspaces are device memory owned by
  *    the caller (e.g. PyTorch tensors), and must stay valid while work that uses them is
- *    in flight.  No call allocates device memory.
+ *    in flight.  No call allocates device memory for data; the cell sort keeps a CUDA
+ *    graph per set of buffers, which the driver instantiates on the first such call
+ *    (see soax_sort_by_cell).
  *  - Streams: every compute call is asynchronous on the given cudaStream_t (passed as
  *    void*; NULL = the legacy default stream) on the calling thread's current device.
  *    Calls do not synchronise with the host, except soax_sync(), soax_autotune() and
@@ -271,9 +273,18 @@ int soax_permute(soax_t h, const uint32_t* perm, void* stream);
 /* Workspace bytes soax_sort_by_cell needs. */
 int soax_sort_workspace_bytes(soax_t h, int32_t grid, size_t* bytes);
 
-/* Cell keys of the field tagged 'P' on a grid^3 grid, stable radix sort, permute-gather
- * of all fields into the shadow set, flip.  The sorted keys and the permutation are left
- * in the workspace (soax_sort_results gives their addresses).
+/* Cell keys of the field tagged 'P' on a grid^3 grid, stable sort, permute-gather of all
+ * fields into the shadow set, flip.  The sorted keys and the permutation are left in the
+ * workspace (soax_sort_results gives their addresses).
+ * The sort (here and in soax_sort_by_keys, soax_sort_perm): for grids up to 64^3 a
+ * counting sort that exploits keys in near-cell order, launched as one CUDA graph whose
+ * conditional node runs the LSD radix passes only for keys the counting sort cannot take
+ * (more than 2048 particles or 256 runs in one cell, keys in no particular order).  The
+ * graph is built on the first call for a set of (keys, sorted keys, permutation,
+ * workspace, n, grid) and kept (the eight most recent sets per process); on a stream
+ * that is being captured into a graph, the same kernels are launched into the capture
+ * with the radix passes gated behind them.  Larger grids: the radix passes alone.  Every
+ * form gives the same stable permutation.
  * Defining passages: spatial locality (Sec. 1, Sec. 2's cache analysis) for the order;
  * apply-to-all-arrays (Listing 7, Sec. 4.2.1) for the gather of every field. */
 int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_bytes, void* stream);

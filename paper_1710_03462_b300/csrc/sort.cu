@@ -13,6 +13,8 @@
 // contiguously.  No block waits on another block, so nothing can hang.
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "cell_key.cuh"
 #include "soax_internal.h"
@@ -1008,17 +1010,8 @@ extern "C" int soax_sort_results(soax_t h, int32_t grid, void* ws, size_t ws_byt
 
 namespace soax {
 
-// The stable argsort of n cell keys on a grid^3 grid into perm (and the sorted keys into
-// skeys unless NULL), in the workspace laid out by sort_ws_plan: the cell counting sort
-// for grids up to 64^3 (the radix passes, gated, behind it for keys it cannot take), the
-// radix sort alone beyond.
-static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, int64_t n, int grid, void* ws,
-                        void* stream) {
-  const SortWs w = sort_ws_plan(n, grid);
-  char* base = static_cast<char*>(ws);
-  if (!w.cell)
-    return radix_sort_gated(keys, nullptr, skeys, perm, n, w.bits, base + w.off_radix, w.rp.total, stream, nullptr);
-  if (!aligned16(keys)) return fail(SOAX_EALIGN, "cell sort: keys not 16-byte aligned");
+static CellSortArgs cell_args(int64_t n, const SortWs& w, char* base, const uint32_t* keys, uint32_t* skeys,
+                              uint32_t* perm) {
   CellSortArgs a;
   a.keys = keys;
   a.n = n;
@@ -1032,7 +1025,14 @@ static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, i
   a.tmp = reinterpret_cast<uint32_t*>(base + w.off_tmp);
   a.perm = perm;
   a.skeys = skeys;
-  cudaStream_t s = as_stream(stream);
+  return a;
+}
+
+// The counting passes of the cell sort on stream s: zeroed header, probe, count, chunk
+// totals, bucket scan, scatter, per-key order (each raises the gate for keys it cannot
+// take and returns at once once it is raised).
+static int cell_counting_passes(const CellSortArgs& a, const SortWs& w, char* base, cudaStream_t s) {
+  const int64_t n = a.n;
   cudaError_t e = cudaMemsetAsync(base + w.off_hdr, 0, w.hdr_bytes, s);
   if (e != cudaSuccess) return cuda_fail(e, "cell sort: memset");
   const int64_t seg_blocks = ((n + 31) / 32 + kSegBatch * (kCellBlock / 32) - 1) / (kSegBatch * (kCellBlock / 32));
@@ -1057,7 +1057,151 @@ static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, i
     k_cell_order<uint32_t><<<go, kCellOrderWarps * 32, 0, s>>>(a);
   else
     k_cell_order<unsigned long long><<<go, kCellOrderWarps * 32, 0, s>>>(a);
-  if (int r = check_launch("cell sort: order")) return r;
+  return check_launch("cell sort: order");
+}
+
+// Opens the body of the graph's conditional node (the radix passes) when the counting
+// passes raised the gate.
+__global__ void k_cell_decide(const int* __restrict__ gate, cudaGraphConditionalHandle h) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, *gate != 0 ? 1u : 0u);
+}
+
+// The cell sort as one CUDA graph per set of pointers and sizes: the counting passes, a
+// one-thread kernel that reads the gate, and the radix passes in the body of an IF node
+// that runs only when the gate is up.  Launched as streams of kernels, the radix passes
+// sit behind the counting sort gated (six launches that return at once, ~16 us at 16.7M
+// keys); in the graph they are not launched at all, and the graph's kernels follow one
+// another with shorter gaps.
+struct CellGraphKey {
+  unsigned long long ctx;
+  const uint32_t* keys;
+  uint32_t* skeys;
+  uint32_t* perm;
+  void* ws;
+  int64_t n;
+  int grid;
+  bool operator==(const CellGraphKey& o) const {
+    return ctx == o.ctx && keys == o.keys && skeys == o.skeys && perm == o.perm && ws == o.ws && n == o.n &&
+           grid == o.grid;
+  }
+};
+
+struct CellGraph {
+  CellGraphKey key;
+  cudaGraphExec_t exec;  // NULL: building failed, launch the kernels on the stream
+};
+
+constexpr size_t kCellGraphCache = 8;
+static std::mutex g_cell_graph_mu;
+static std::vector<CellGraph> g_cell_graphs;  // most recently used first
+thread_local bool t_cell_graph_off = false;
+
+// Captures the graph on a private stream.  Any failure leaves *out NULL.
+static void build_cell_graph(const CellSortArgs& a, const SortWs& w, char* base, cudaGraphExec_t* out) {
+  *out = nullptr;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle hnd;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&hnd, g, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+            cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  bool capturing = ok;
+  cudaGraphNodeParams cp = {};
+  if (ok) ok = cell_counting_passes(a, w, base, cs) == SOAX_OK;
+  if (ok) {
+    k_cell_decide<<<1, 32, 0, cs>>>(a.gate, hnd);
+    ok = cudaGetLastError() == cudaSuccess;
+  }
+  if (ok) {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNode_t cn;
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hnd;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    ok = cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
+         st == cudaStreamCaptureStatusActive &&
+         cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp) == cudaSuccess &&
+         cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) == cudaSuccess;
+  }
+  if (capturing) {
+    cudaGraph_t done = nullptr;
+    ok = cudaStreamEndCapture(cs, &done) == cudaSuccess && ok;
+  }
+  if (ok) {  // the body: the radix passes, ungated
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      ok = radix_sort_gated(a.keys, nullptr, a.skeys, a.perm, a.n, w.bits, base + w.off_radix, w.rp.total, cs,
+                            nullptr) == SOAX_OK;
+      cudaGraph_t done = nullptr;
+      ok = cudaStreamEndCapture(cs, &done) == cudaSuccess && ok;
+    }
+  }
+  if (ok) ok = cudaGraphInstantiate(out, g, 0) == cudaSuccess;
+  if (!ok) *out = nullptr;
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  cudaGetLastError();  // a failed build falls back to the stream form, leaving no error behind
+}
+
+// The cached graph for these pointers and sizes (built on first use), or NULL.
+static cudaGraphExec_t cell_graph(const CellSortArgs& a, const SortWs& w, char* base, int grid) {
+  const CellGraphKey key{current_context_id(), a.keys, a.skeys, a.perm, base, a.n, grid};
+  std::lock_guard<std::mutex> lk(g_cell_graph_mu);
+  for (size_t i = 0; i < g_cell_graphs.size(); ++i) {
+    if (g_cell_graphs[i].key == key) {
+      const CellGraph hit = g_cell_graphs[i];
+      g_cell_graphs.erase(g_cell_graphs.begin() + i);
+      g_cell_graphs.insert(g_cell_graphs.begin(), hit);
+      return hit.exec;
+    }
+  }
+  CellGraph gnew{key, nullptr};
+  build_cell_graph(a, w, base, &gnew.exec);
+  if (g_cell_graphs.size() >= kCellGraphCache) {
+    // An executable graph still running is freed when it completes.
+    if (g_cell_graphs.back().exec) cudaGraphExecDestroy(g_cell_graphs.back().exec);
+    g_cell_graphs.pop_back();
+  }
+  g_cell_graphs.insert(g_cell_graphs.begin(), gnew);
+  return gnew.exec;
+}
+
+// Whether the calling thread's cell sorts launch their kernels on the stream instead of
+// a graph (for callers that must not create graphs); returns the previous setting.
+bool set_cell_graph_off(bool off) {
+  const bool prev = t_cell_graph_off;
+  t_cell_graph_off = off;
+  return prev;
+}
+
+// The stable argsort of n cell keys on a grid^3 grid into perm (and the sorted keys into
+// skeys unless NULL), in the workspace laid out by sort_ws_plan: the cell counting sort
+// for grids up to 64^3 (the radix passes behind it for keys it cannot take: in the body
+// of a graph's conditional node, or gated on the stream when the caller's stream is
+// being captured or graphs are off), the radix sort alone beyond.
+static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, int64_t n, int grid, void* ws,
+                        void* stream) {
+  const SortWs w = sort_ws_plan(n, grid);
+  char* base = static_cast<char*>(ws);
+  if (!w.cell)
+    return radix_sort_gated(keys, nullptr, skeys, perm, n, w.bits, base + w.off_radix, w.rp.total, stream, nullptr);
+  if (!aligned16(keys)) return fail(SOAX_EALIGN, "cell sort: keys not 16-byte aligned");
+  const CellSortArgs a = cell_args(n, w, base, keys, skeys, perm);
+  cudaStream_t s = as_stream(stream);
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  if (!t_cell_graph_off && cudaStreamIsCapturing(s, &cst) == cudaSuccess && cst == cudaStreamCaptureStatusNone) {
+    if (cudaGraphExec_t ex = cell_graph(a, w, base, grid)) {
+      const cudaError_t e = cudaGraphLaunch(ex, s);
+      return e == cudaSuccess ? SOAX_OK : cuda_fail(e, "cell sort: graph launch");
+    }
+  }
+  if (int r = cell_counting_passes(a, w, base, s)) return r;
   return radix_sort_gated(keys, nullptr, skeys, perm, n, w.bits, base + w.off_radix, w.rp.total, stream, a.gate);
 }
 

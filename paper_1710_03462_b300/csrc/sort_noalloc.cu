@@ -35,6 +35,10 @@ int noalloc_scratch(void** out) {
 
 }  // namespace
 
+namespace soax {
+bool set_cell_graph_off(bool off);  // sort.cu
+}  // namespace soax
+
 extern "C" int soax_sort_by_cell_noalloc(soax_t h, int32_t grid, uint32_t* perm_out, void* stream) {
   using namespace soax;
   if (int r = check_handle(h)) return r;
@@ -51,8 +55,12 @@ extern "C" int soax_sort_by_cell_noalloc(soax_t h, int32_t grid, uint32_t* perm_
   if (int r = noalloc_scratch(&ws)) return r;
   // The sort clears what it counts into (the cell sort's counts and gate, the radix
   // sort's per-pass digit totals) itself; every other part of the scratch is fully
-  // written before it is read, so nothing left from an earlier call is used.
-  if (int r = soax_sort_by_cell(h, grid, ws, kNoAllocScratchBytes, stream)) return r;
+  // written before it is read, so nothing left from an earlier call is used.  Its kernels
+  // go on the stream, not into a CUDA graph (instantiating one is an allocation).
+  const bool prev = set_cell_graph_off(true);
+  const int rs = soax_sort_by_cell(h, grid, ws, kNoAllocScratchBytes, stream);
+  set_cell_graph_off(prev);
+  if (rs) return rs;
   if (perm_out) {
     uint32_t* perm = nullptr;
     if (int r = soax_sort_results(h, grid, ws, kNoAllocScratchBytes, nullptr, &perm)) return r;

@@ -75,6 +75,6 @@ def test_source_hash_ignores_comments_only():
 
 
 def test_sort_kernel_launches():
-    assert bench.sort_kernel_launches(32) == 6 + 6   # 15 bits: counting sort + 2 gated radix passes
-    assert bench.sort_kernel_launches(64) == 6 + 6   # 18 bits
+    assert bench.sort_kernel_launches(32) == 6 + 1   # 15 bits: counting sort + the conditional's kernel
+    assert bench.sort_kernel_launches(64) == 6 + 1   # 18 bits
     assert bench.sort_kernel_launches(100) == 9      # 20 bits: the radix passes alone

@@ -119,3 +119,68 @@ def test_unordered_then_near_sorted_sets():
     _, perm = p.sort_perm(grid, keys, ws)
     sx.sync()
     assert np.array_equal(_u32(perm), oracle.stable_argsort(_u32(keys).copy())[0])
+
+
+def test_graph_reused_across_key_sets_in_the_same_buffers():
+    """One graph serves every call with the same pointers and sizes: the same key buffer
+    filled with near-sorted keys, keys beyond the per-key capacity (the conditional body
+    runs the radix passes) and near-sorted keys again."""
+    n, grid = 200003, 32
+    rng = np.random.default_rng(17)
+    p = sx.Particles([("pos", "f64", 3, "P")], n)
+    ws = p.sort_workspace(grid)
+    kt = torch.empty(n, dtype=torch.int32, device="cuda")
+    base = np.sort(rng.integers(0, grid ** 3, n, dtype=np.uint32))
+    crowded = base.copy()
+    crowded[rng.random(n) < 0.3] = 777
+    for keys in (base, crowded, np.roll(base, 5000), crowded[::-1].copy(), base):
+        kt.copy_(torch.from_numpy(keys.view(np.int32)))
+        _, perm = p.sort_perm(grid, kt, ws)
+        sx.sync()
+        assert np.array_equal(_u32(perm), oracle.stable_argsort(keys)[0])
+
+
+def test_more_pointer_sets_than_the_graph_cache():
+    """Ten workspaces used in turn, twice (more than the graphs kept): each call still
+    gives the oracle's permutation."""
+    n, grid = 50001, 16
+    rng = np.random.default_rng(18)
+    p = sx.Particles([("pos", "f64", 3, "P")], n)
+    wss = [p.sort_workspace(grid) for _ in range(10)]
+    kt = torch.empty(n, dtype=torch.int32, device="cuda")
+    for rep in range(2):
+        for j, ws in enumerate(wss):
+            keys = np.sort(rng.integers(0, grid ** 3, n, dtype=np.uint32))
+            if (j + rep) % 3 == 0:
+                keys = rng.permutation(keys)  # in no particular order: the radix passes
+            kt.copy_(torch.from_numpy(keys.view(np.int32)))
+            _, perm = p.sort_perm(grid, kt, ws)
+            sx.sync()
+            assert np.array_equal(_u32(perm), oracle.stable_argsort(keys)[0]), (rep, j)
+
+
+def test_sort_inside_a_captured_graph():
+    """A caller capturing its own CUDA graph gets the sort's kernels on its stream (the
+    radix passes gated): replays of the captured sort give the oracle's permutation for
+    the keys in the buffer at replay time."""
+    n, grid = 100003, 32
+    rng = np.random.default_rng(19)
+    p = sx.Particles([("pos", "f64", 3, "P")], n)
+    ws = p.sort_workspace(grid)
+    kt = torch.empty(n, dtype=torch.int32, device="cuda")
+    kt.copy_(torch.from_numpy(np.sort(rng.integers(0, grid ** 3, n, dtype=np.uint32)).view(np.int32)))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        p.sort_perm(grid, kt, ws, stream=s)  # builds nothing: warm-up outside the capture
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        _, perm = p.sort_perm(grid, kt, ws, stream=s)
+    for keys in (np.sort(rng.integers(0, grid ** 3, n, dtype=np.uint32)),
+                 rng.integers(0, grid ** 3, n, dtype=np.uint32)):
+        kt.copy_(torch.from_numpy(keys.view(np.int32)))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(_u32(perm), oracle.stable_argsort(keys)[0])
