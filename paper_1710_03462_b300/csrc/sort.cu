@@ -375,9 +375,9 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermArg
 //            index there.
 // A key with more than kCellMaxParticles particles (found by the scan) or more than
 // kCellMaxGroups chunks (found by the order kernel) does not fit the per-warp buffers:
-// the gate is raised and the radix passes (launched after, gated) sort instead of this
-// sort; scatter and order return at once once it is raised.  Nothing waits on another
-// block.
+// the gate is raised and the radix passes (behind the counting sort: in a graph's
+// conditional node, or launched gated) sort instead of this sort; scatter and order
+// return at once once it is raised.  Nothing waits on another block.
 constexpr int kCellMaxParticles = 2048;  // per key: the per-warp chunk-id table
 constexpr int kCellMaxGroups = 256;      // per key: 8 chunk keys per lane in the warp sort
 constexpr int kCellChunk = 4096;         // keys per scan block

@@ -1,9 +1,12 @@
 """The cell counting sort (grids up to 64^3: counts, bucket scan, scatter of equal-key
-groups, per-key order of the groups by segment) and its gated fallback to the radix
-passes, bit-exact against the oracle's stable argsort: near-sorted keys (the bench's
-case: a sorted set stepped again), random keys, keys at the per-key capacity (2048
-particles, 256 groups), keys beyond it (one key holding most particles: the radix passes
-sort), tiny and ragged sizes, and the sorted keys written beside the permutation."""
+groups, per-key order of the groups by segment) and its fallback to the radix passes
+(the body of the sort graph's conditional node, or gated on a stream being captured),
+bit-exact against the oracle's stable argsort: near-sorted keys (the bench's case: a
+sorted set stepped again), random keys, keys at the per-key capacity (2048 particles,
+256 groups), keys beyond it (one key holding most particles: the radix passes sort),
+tiny and ragged sizes, the sorted keys written beside the permutation, one graph serving
+many key sets, more buffer sets than the graph cache, and the sort inside a caller's
+captured graph."""
 import numpy as np
 import pytest
 import torch
