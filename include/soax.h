@@ -305,6 +305,12 @@ int soax_sort_by_keys(soax_t h, int32_t grid, const uint32_t* keys, void* ws, si
  * Defining passages: as for soax_sort_by_cell (the order only). */
 int soax_sort_perm(soax_t h, int32_t grid, const uint32_t* keys, void* ws, size_t ws_bytes, void* stream);
 
+/* How many cell-sort graphs this process has built (*built) and how many builds failed
+ * (*failed: those sets of buffers launch the same kernels on the stream instead, with
+ * the radix passes gated).  A diagnostic for callers and tests; see soax_sort_by_cell.
+ * Defining passages: as for soax_sort_by_cell. */
+int soax_sort_graph_counts(int64_t* built, int64_t* failed);
+
 /* soax_sort_by_cell without a caller workspace.  The paper has no counterpart: this is
  * for hosts that cannot allocate device memory where they sort -- C or Fortran codes
  * linking the library with no device allocator of their own, or time-step loops that

@@ -554,6 +554,14 @@ class Particles:
         return loss, xb
 
 
+def sort_graph_counts():
+    """(built, failed): the cell-sort CUDA graphs this process built, and the builds that
+    failed (those sorts launch their kernels on the stream) (soax_sort_graph_counts)."""
+    built, failed = C.c_int64(), C.c_int64()
+    _check(lib().soax_sort_graph_counts(C.byref(built), C.byref(failed)), "soax_sort_graph_counts")
+    return built.value, failed.value
+
+
 def radix_sort_pairs(keys, vals=None, key_bits=32, want_keys=True, ws=None, stream=None, out=None):
     """Stable LSD radix sort of (u32 key, u32 value); vals None = argsort.  Tensors are
     int32 holding the u32 bit patterns.  Returns (sorted keys or None, sorted values);

@@ -68,6 +68,7 @@ SIGNATURES = {
     "soax_sort_workspace_bytes": [_p, _i32, _P(_sz)],
     "soax_sort_by_keys": [_p, _i32, _p, _p, _sz, _p],
     "soax_sort_perm": [_p, _i32, _p, _p, _sz, _p],
+    "soax_sort_graph_counts": [_P(C.c_int64), _P(C.c_int64)],
     "soax_sort_by_cell": [_p, _i32, _p, _sz, _p],
     "soax_sort_results": [_p, _i32, _p, _sz, _P(_p), _P(_p)],
     "soax_sort_by_cell_noalloc": [_p, _i32, _p, _p],

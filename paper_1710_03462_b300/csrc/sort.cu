@@ -865,6 +865,27 @@ extern "C" int soax_radix_sort_pairs(const uint32_t* keys_in, const uint32_t* va
 }
 
 namespace soax {
+// The downsweep's shared memory above 48 KB and the largest carveout, set once per device.
+static int radix_prepare() {
+  static std::mutex mu;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return SOAX_OK;
+  std::lock_guard<std::mutex> lk(mu);
+  if (attr_set[dev]) return SOAX_OK;
+  for (const void* fn : {(const void*)k_radix_downsweep<false>, (const void*)k_radix_downsweep<true>}) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)downsweep_smem(kMaxRadix));
+    // Prefer shared memory over L1 so that three 53 KB blocks fit on an SM.
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: smem attribute");
+  }
+  attr_set[dev] = true;
+  return SOAX_OK;
+}
+
 // The radix sort; gate as for the kernels (NULL: always sort).
 static int radix_sort_gated(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                             int64_t n, int32_t key_bits, void* ws, size_t ws_bytes, void* stream, const int* gate) {
@@ -878,21 +899,7 @@ static int radix_sort_gated(const uint32_t* keys_in, const uint32_t* vals_in, ui
     return fail(SOAX_EINVAL, "soax_radix_sort_pairs: outputs must not alias inputs");
   RadixPlan p = radix_plan(n, key_bits);
   if (ws_bytes < p.total) return fail(SOAX_ENOMEM, "soax_radix_sort_pairs: workspace too small");
-  static bool attr_set[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    for (const void* fn : {(const void*)k_radix_downsweep<false>, (const void*)k_radix_downsweep<true>}) {
-      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)downsweep_smem(kMaxRadix));
-      // Prefer shared memory over L1 so that three 53 KB blocks fit on an SM.
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-      if (e != cudaSuccess) return cuda_fail(e, "soax_radix_sort_pairs: smem attribute");
-    }
-    attr_set[dev] = true;
-  }
+  if (int r = radix_prepare()) return r;
   char* w = static_cast<char*>(ws);
   uint32_t* counts = reinterpret_cast<uint32_t*>(w + p.off_counts);
   uint32_t* totals = reinterpret_cast<uint32_t*>(w + p.off_totals);
@@ -1094,11 +1101,13 @@ struct CellGraph {
 constexpr size_t kCellGraphCache = 8;
 static std::mutex g_cell_graph_mu;
 static std::vector<CellGraph> g_cell_graphs;  // most recently used first
+static int64_t g_cell_graphs_built = 0, g_cell_graphs_failed = 0;
 thread_local bool t_cell_graph_off = false;
 
 // Captures the graph on a private stream.  Any failure leaves *out NULL.
 static void build_cell_graph(const CellSortArgs& a, const SortWs& w, char* base, cudaGraphExec_t* out) {
   *out = nullptr;
+  if (radix_prepare() != SOAX_OK) return;  // function attributes before the capture
   cudaStream_t cs = nullptr;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return;
   cudaGraph_t g = nullptr;
@@ -1163,6 +1172,7 @@ static cudaGraphExec_t cell_graph(const CellSortArgs& a, const SortWs& w, char* 
   }
   CellGraph gnew{key, nullptr};
   build_cell_graph(a, w, base, &gnew.exec);
+  ++(gnew.exec ? g_cell_graphs_built : g_cell_graphs_failed);
   if (g_cell_graphs.size() >= kCellGraphCache) {
     // An executable graph still running is freed when it completes.
     if (g_cell_graphs.back().exec) cudaGraphExecDestroy(g_cell_graphs.back().exec);
@@ -1261,4 +1271,12 @@ extern "C" int soax_sort_by_cell(soax_t h, int32_t grid, void* ws, size_t ws_byt
   uint32_t* keys = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + w.off_keys);
   if (int r = soax_cell_keys(h, pf, grid, keys, stream)) return r;
   return sort_by_keys_impl(h, grid, keys, ws, stream);
+}
+
+extern "C" int soax_sort_graph_counts(int64_t* built, int64_t* failed) {
+  if (!built || !failed) return soax::fail(SOAX_EINVAL, "soax_sort_graph_counts: NULL");
+  std::lock_guard<std::mutex> lk(soax::g_cell_graph_mu);
+  *built = soax::g_cell_graphs_built;
+  *failed = soax::g_cell_graphs_failed;
+  return SOAX_OK;
 }

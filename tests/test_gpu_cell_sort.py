@@ -127,7 +127,8 @@ def test_unordered_then_near_sorted_sets():
 def test_graph_reused_across_key_sets_in_the_same_buffers():
     """One graph serves every call with the same pointers and sizes: the same key buffer
     filled with near-sorted keys, keys beyond the per-key capacity (the conditional body
-    runs the radix passes) and near-sorted keys again."""
+    runs the radix passes) and near-sorted keys again.  Exactly one graph is built for
+    the five calls, and no build fails."""
     n, grid = 200003, 32
     rng = np.random.default_rng(17)
     p = sx.Particles([("pos", "f64", 3, "P")], n)
@@ -136,11 +137,14 @@ def test_graph_reused_across_key_sets_in_the_same_buffers():
     base = np.sort(rng.integers(0, grid ** 3, n, dtype=np.uint32))
     crowded = base.copy()
     crowded[rng.random(n) < 0.3] = 777
+    built0, failed0 = sx.sort_graph_counts()
     for keys in (base, crowded, np.roll(base, 5000), crowded[::-1].copy(), base):
         kt.copy_(torch.from_numpy(keys.view(np.int32)))
         _, perm = p.sort_perm(grid, kt, ws)
         sx.sync()
         assert np.array_equal(_u32(perm), oracle.stable_argsort(keys)[0])
+    built1, failed1 = sx.sort_graph_counts()
+    assert (built1 - built0, failed1 - failed0) == (1, 0)
 
 
 def test_more_pointer_sets_than_the_graph_cache():
@@ -175,11 +179,13 @@ def test_sort_inside_a_captured_graph():
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        p.sort_perm(grid, kt, ws, stream=s)  # builds nothing: warm-up outside the capture
+        p.sort_perm(grid, kt, ws, stream=s)  # warm-up outside the capture (builds the sort's graph)
     s.synchronize()
+    counts = sx.sort_graph_counts()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         _, perm = p.sort_perm(grid, kt, ws, stream=s)
+    assert sx.sort_graph_counts() == counts  # inside the capture: no graph built
     for keys in (np.sort(rng.integers(0, grid ** 3, n, dtype=np.uint32)),
                  rng.integers(0, grid ** 3, n, dtype=np.uint32)):
         kt.copy_(torch.from_numpy(keys.view(np.int32)))
