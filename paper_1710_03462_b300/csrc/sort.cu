@@ -1158,28 +1158,43 @@ static void build_cell_graph(const CellSortArgs& a, const SortWs& w, char* base,
   cudaGetLastError();  // a failed build falls back to the stream form, leaving no error behind
 }
 
-// The cached graph for these pointers and sizes (built on first use), or NULL.
-static cudaGraphExec_t cell_graph(const CellSortArgs& a, const SortWs& w, char* base, int grid) {
+// Launches the cached graph for these pointers and sizes (built on first use) on s; sets
+// *launched to false when there is none (its build failed).  The launch happens under
+// the cache's lock, so another thread cannot evict and destroy the graph in between.
+static int cell_graph_launch(const CellSortArgs& a, const SortWs& w, char* base, int grid, cudaStream_t s,
+                             bool* launched) {
+  *launched = false;
   const CellGraphKey key{current_context_id(), a.keys, a.skeys, a.perm, base, a.n, grid};
   std::lock_guard<std::mutex> lk(g_cell_graph_mu);
+  cudaGraphExec_t ex = nullptr;
+  bool found = false;
   for (size_t i = 0; i < g_cell_graphs.size(); ++i) {
     if (g_cell_graphs[i].key == key) {
       const CellGraph hit = g_cell_graphs[i];
       g_cell_graphs.erase(g_cell_graphs.begin() + i);
       g_cell_graphs.insert(g_cell_graphs.begin(), hit);
-      return hit.exec;
+      ex = hit.exec;
+      found = true;
+      break;
     }
   }
-  CellGraph gnew{key, nullptr};
-  build_cell_graph(a, w, base, &gnew.exec);
-  ++(gnew.exec ? g_cell_graphs_built : g_cell_graphs_failed);
-  if (g_cell_graphs.size() >= kCellGraphCache) {
-    // An executable graph still running is freed when it completes.
-    if (g_cell_graphs.back().exec) cudaGraphExecDestroy(g_cell_graphs.back().exec);
-    g_cell_graphs.pop_back();
+  if (!found) {
+    CellGraph gnew{key, nullptr};
+    build_cell_graph(a, w, base, &gnew.exec);
+    ++(gnew.exec ? g_cell_graphs_built : g_cell_graphs_failed);
+    if (g_cell_graphs.size() >= kCellGraphCache) {
+      // An executable graph still running is freed when it completes.
+      if (g_cell_graphs.back().exec) cudaGraphExecDestroy(g_cell_graphs.back().exec);
+      g_cell_graphs.pop_back();
+    }
+    g_cell_graphs.insert(g_cell_graphs.begin(), gnew);
+    ex = gnew.exec;
   }
-  g_cell_graphs.insert(g_cell_graphs.begin(), gnew);
-  return gnew.exec;
+  if (!ex) return SOAX_OK;
+  const cudaError_t e = cudaGraphLaunch(ex, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cell sort: graph launch");
+  *launched = true;
+  return SOAX_OK;
 }
 
 // Whether the calling thread's cell sorts launch their kernels on the stream instead of
@@ -1206,10 +1221,9 @@ static int cell_argsort(const uint32_t* keys, uint32_t* skeys, uint32_t* perm, i
   cudaStream_t s = as_stream(stream);
   cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
   if (!t_cell_graph_off && cudaStreamIsCapturing(s, &cst) == cudaSuccess && cst == cudaStreamCaptureStatusNone) {
-    if (cudaGraphExec_t ex = cell_graph(a, w, base, grid)) {
-      const cudaError_t e = cudaGraphLaunch(ex, s);
-      return e == cudaSuccess ? SOAX_OK : cuda_fail(e, "cell sort: graph launch");
-    }
+    bool launched = false;
+    if (int r = cell_graph_launch(a, w, base, grid, s, &launched)) return r;
+    if (launched) return SOAX_OK;
   }
   if (int r = cell_counting_passes(a, w, base, s)) return r;
   return radix_sort_gated(keys, nullptr, skeys, perm, n, w.bits, base + w.off_radix, w.rp.total, stream, a.gate);

@@ -193,3 +193,44 @@ def test_sort_inside_a_captured_graph():
         g.replay()
         torch.cuda.synchronize()
         assert np.array_equal(_u32(perm), oracle.stable_argsort(keys)[0])
+
+
+def test_two_threads_sharing_the_graph_cache():
+    """Two host threads sort on their own streams with six workspaces each (twelve
+    buffer sets against a cache of eight: graphs are evicted while the other thread
+    launches its own); every permutation is the oracle's."""
+    import threading
+
+    n, grid = 40009, 16
+    errors = []
+
+    def worker(seed):
+        try:
+            rng = np.random.default_rng(seed)
+            s = torch.cuda.Stream()
+            p = sx.Particles([("pos", "f64", 3, "P")], n)
+            wss = [p.sort_workspace(grid) for _ in range(6)]
+            kt = torch.empty(n, dtype=torch.int32, device="cuda")
+            torch.cuda.synchronize()
+            for rep in range(3):
+                for j, ws in enumerate(wss):
+                    keys = np.sort(rng.integers(0, grid ** 3, n, dtype=np.uint32))
+                    if (j + rep) % 4 == 0:
+                        keys = rng.permutation(keys)
+                    with torch.cuda.stream(s):
+                        kt.copy_(torch.from_numpy(keys.view(np.int32)))
+                        _, perm = p.sort_perm(grid, kt, ws, stream=s)
+                        got = perm.cpu()  # on s: after the sort
+                    s.synchronize()
+                    if not np.array_equal(got.numpy().view(np.uint32), oracle.stable_argsort(keys)[0]):
+                        errors.append((seed, rep, j))
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(s,)) for s in (31, 32)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    sx.sync()
